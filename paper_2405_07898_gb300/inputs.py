@@ -1,0 +1,300 @@
+"""Seeded synthetic inputs for the EAM timestep: lattices, thermal states and
+potential knot tables.
+
+This module is shared by the CUDA path, the CPU oracle, the tests and the
+benchmark.  It holds none of the method's arithmetic: it only produces the
+*inputs* the method consumes (positions, velocities, types, masses and the
+knot values of the three EAM functions).  Spline construction, neighbour
+search, density, forces, energies and integration are each implemented
+separately on the two sides.
+
+Units are metal units throughout: Angstrom, eV, amu, fs, K.
+
+The paper (Section "Computational Molecular Dynamics", Eqs. 2-4) lets rho_i,
+F_i and phi_ij be arbitrary splines per atom type; its own benchmarks use
+published Cu/W/Ta potentials that are not available here.  The stand-in is
+the analytic Johnson form
+
+    f(r)   = fe * exp(-beta  * (r/re - 1))
+    phi(r) = A  * exp(-alpha * (r/re - 1)) - B * exp(-kappa * (r/re - 1))
+    F(rho) = -E0 * sqrt(rho / rho_e)
+
+with f and phi multiplied by a quintic smoothstep that takes them to zero,
+with two continuous derivatives, between r_s = r_cut - 0.5 and r_cut
+(the paper only states that the functions vanish beyond the cutoff).
+The BCC parameter set (a = 3.30, m = 180.95, r_cut = 4.5) stands in for the
+Ta system of Table "Results for 800,000 atom models" (14 interactions per
+atom, as there); the FCC set (a = 3.615, m = 63.55, r_cut = 5.0) stands in
+for Cu (42 interactions per atom).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# 1 eV/(Angstrom*amu) expressed in Angstrom/fs^2 (CODATA 2018 e and u).
+ACCEL_EV_A_AMU = 9.648533215665e-3
+# Boltzmann constant in eV/K.
+KB_EV = 8.617333262e-5
+
+SEED_BASE = 7898
+
+BC_NATURAL = 0
+BC_CLAMPED = 1
+
+
+@dataclasses.dataclass(frozen=True)
+class JohnsonParams:
+    """Parameters of one analytic Johnson-form EAM species."""
+    name: str
+    lattice: str          # "bcc" or "fcc"
+    a: float              # lattice constant, Angstrom
+    mass: float           # amu
+    re: float = 2.86
+    alpha: float = 8.5
+    beta: float = 4.5
+    kappa: float = 4.5
+    A: float = 0.6
+    B: float = 0.8
+    fe: float = 1.0
+    E0: float = 3.0
+    rho_e: float = 14.0
+    r_cut: float = 4.5
+    smooth_width: float = 0.5
+    skin: float = 0.3
+
+    @property
+    def r_s(self) -> float:
+        return self.r_cut - self.smooth_width
+
+    @property
+    def rho_max(self) -> float:
+        return 3.0 * self.rho_e
+
+
+BCC_TA_LIKE = JohnsonParams(name="bcc_johnson", lattice="bcc", a=3.30, mass=180.95)
+FCC_CU_LIKE = JohnsonParams(name="fcc_johnson", lattice="fcc", a=3.615, mass=63.55,
+                            re=2.55, E0=3.5, r_cut=5.0)
+
+
+def smoothstep(r, r_s, r_c):
+    """Quintic switch: 1 below r_s, 0 at and above r_c, C2 at both ends."""
+    u = np.clip((np.asarray(r, dtype=np.float64) - r_s) / (r_c - r_s), 0.0, 1.0)
+    return 1.0 - 10.0 * u**3 + 15.0 * u**4 - 6.0 * u**5
+
+
+def johnson_f(p: JohnsonParams, r):
+    r = np.asarray(r, dtype=np.float64)
+    return p.fe * np.exp(-p.beta * (r / p.re - 1.0)) * smoothstep(r, p.r_s, p.r_cut)
+
+
+def johnson_phi(p: JohnsonParams, r):
+    r = np.asarray(r, dtype=np.float64)
+    raw = p.A * np.exp(-p.alpha * (r / p.re - 1.0)) - p.B * np.exp(-p.kappa * (r / p.re - 1.0))
+    return raw * smoothstep(r, p.r_s, p.r_cut)
+
+
+def johnson_F(p: JohnsonParams, rho):
+    rho = np.asarray(rho, dtype=np.float64)
+    return -p.E0 * np.sqrt(np.maximum(rho, 0.0) / p.rho_e)
+
+
+def johnson_f_slope0(p: JohnsonParams) -> float:
+    """df/dr at r = 0 (the switch is identically 1 there)."""
+    return -p.beta / p.re * p.fe * math.exp(p.beta)
+
+
+def johnson_phi_slope0(p: JohnsonParams) -> float:
+    return (-p.alpha / p.re * p.A * math.exp(p.alpha)
+            + p.kappa / p.re * p.B * math.exp(p.kappa))
+
+
+@dataclasses.dataclass
+class Knots:
+    """Values of one function on a uniform grid x0 + k*dx, k = 0..n-1, with
+    the end conditions a cubic spline through them should take:
+    BC_NATURAL (zero second derivative) or BC_CLAMPED (given slope)."""
+    x0: float
+    dx: float
+    y: np.ndarray
+    bc_lo: int = BC_NATURAL
+    bc_hi: int = BC_NATURAL
+    d_lo: float = 0.0
+    d_hi: float = 0.0
+
+    @property
+    def n(self) -> int:
+        return int(self.y.shape[0])
+
+    @property
+    def x(self) -> np.ndarray:
+        return self.x0 + self.dx * np.arange(self.n, dtype=np.float64)
+
+
+@dataclasses.dataclass
+class Potential:
+    """A multi-type EAM potential given as knot tables.
+
+    F[t], f[t] belong to type t (f is the density an atom of type t
+    contributes to its neighbours); phi is packed over type pairs a <= b in
+    row-major upper-triangular order."""
+    mass: np.ndarray
+    F: list
+    f: list
+    phi: list
+    r_cut: float
+    skin: float
+
+    @property
+    def ntypes(self) -> int:
+        return len(self.F)
+
+    @property
+    def r_list(self) -> float:
+        return self.r_cut + self.skin
+
+
+def johnson_knots(p: JohnsonParams, n_knots: int = 2000):
+    """Tabulate the three Johnson functions on uniform knots.
+
+    f, phi: r in [0, r_cut], clamped at r = 0 with the analytic slope,
+    natural at r_cut (where the smoothed functions have zero curvature).
+    F: rho in [0, 3 rho_e], natural at both ends."""
+    dr = p.r_cut / (n_knots - 1)
+    r = dr * np.arange(n_knots, dtype=np.float64)
+    f = Knots(0.0, dr, johnson_f(p, r), BC_CLAMPED, BC_NATURAL, johnson_f_slope0(p), 0.0)
+    phi = Knots(0.0, dr, johnson_phi(p, r), BC_CLAMPED, BC_NATURAL, johnson_phi_slope0(p), 0.0)
+    # exact zeros at the cutoff knot (the switch is 0 there)
+    f.y[-1] = 0.0
+    phi.y[-1] = 0.0
+    drho = p.rho_max / (n_knots - 1)
+    rho = drho * np.arange(n_knots, dtype=np.float64)
+    F = Knots(0.0, drho, johnson_F(p, rho), BC_NATURAL, BC_NATURAL)
+    return F, f, phi
+
+
+def johnson_potential(p: JohnsonParams, n_knots: int = 2000) -> Potential:
+    F, f, phi = johnson_knots(p, n_knots)
+    return Potential(mass=np.array([p.mass]), F=[F], f=[f], phi=[phi],
+                     r_cut=p.r_cut, skin=p.skin)
+
+
+# --------------------------------------------------------------------------
+# lattices and thermal states
+
+
+def bcc_lattice(nx: int, ny: int, nz: int, a: float):
+    base = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.5]])
+    return _lattice(base, nx, ny, nz, a)
+
+
+def fcc_lattice(nx: int, ny: int, nz: int, a: float):
+    base = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.0], [0.5, 0.0, 0.5], [0.0, 0.5, 0.5]])
+    return _lattice(base, nx, ny, nz, a)
+
+
+def _lattice(base, nx, ny, nz, a):
+    ix, iy, iz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    cells = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1).astype(np.float64)
+    pos = (cells[:, None, :] + base[None, :, :]).reshape(-1, 3) * a
+    box = np.array([nx * a, ny * a, nz * a], dtype=np.float64)
+    return np.ascontiguousarray(pos), box
+
+
+def lattice(p: JohnsonParams, nx: int, ny: int, nz: int):
+    return bcc_lattice(nx, ny, nz, p.a) if p.lattice == "bcc" else fcc_lattice(nx, ny, nz, p.a)
+
+
+def displace(pos, box, sigma: float, rng: np.random.Generator):
+    """Gaussian displacement of every coordinate, re-wrapped into the box."""
+    out = pos + rng.normal(0.0, sigma, size=pos.shape)
+    return np.ascontiguousarray(np.mod(out, box))
+
+
+def maxwell(n: int, mass, temperature: float, rng: np.random.Generator):
+    """Maxwell-Boltzmann velocities (Angstrom/fs) with zero total momentum,
+    rescaled so that the kinetic temperature over 3N-3 degrees of freedom is
+    exactly `temperature`."""
+    m = np.broadcast_to(np.asarray(mass, dtype=np.float64), (n,)).astype(np.float64)
+    if n < 2 or temperature <= 0.0:
+        return np.zeros((n, 3))
+    sd = np.sqrt(KB_EV * temperature * ACCEL_EV_A_AMU / m)
+    v = rng.normal(size=(n, 3)) * sd[:, None]
+    v -= (m[:, None] * v).sum(axis=0) / m.sum()
+    ke = 0.5 * (m[:, None] * v * v).sum() / ACCEL_EV_A_AMU
+    t_now = 2.0 * ke / ((3 * n - 3) * KB_EV)
+    v *= math.sqrt(temperature / t_now)
+    return np.ascontiguousarray(v)
+
+
+@dataclasses.dataclass
+class System:
+    """One periodic system: the inputs md_create takes."""
+    box: np.ndarray
+    pos: np.ndarray
+    vel: np.ndarray
+    types: np.ndarray
+    pot: Potential
+    label: str = ""
+
+    @property
+    def n(self) -> int:
+        return int(self.pos.shape[0])
+
+
+def thermal_system(p: JohnsonParams, cells, sigma: float, temperature: float, seed: int,
+                   n_knots: int = 2000, label: str = "") -> System:
+    pos, box = lattice(p, *cells)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pos = displace(pos, box, sigma, rng)
+    vel = maxwell(pos.shape[0], p.mass, temperature, rng)
+    types = np.zeros(pos.shape[0], dtype=np.int32)
+    return System(box=box, pos=pos, vel=vel, types=types, pot=johnson_potential(p, n_knots),
+                  label=label or f"{p.lattice}{cells[0]}x{cells[1]}x{cells[2]}")
+
+
+# --------------------------------------------------------------------------
+# the named workloads
+
+
+def bcc_2000_fp64() -> System:
+    """2,000-atom BCC cube (10x10x10 cells, a = 3.30, L = 33 A), sigma 0.02 A,
+    300 K, 2,000-knot tables; integrated 100 steps at dt = 2 fs in FP64."""
+    return thermal_system(BCC_TA_LIKE, (10, 10, 10), 0.02, 300.0, SEED_BASE + 0,
+                          label="bcc_2000")
+
+
+def bcc_799496() -> System:
+    """799,496-atom BCC system (74x74x73 cells; box 244.2 x 244.2 x 240.9 A),
+    sigma 0.02 A, 300 K: the 800k-atom mixed-precision workload."""
+    return thermal_system(BCC_TA_LIKE, (74, 74, 73), 0.02, 300.0, SEED_BASE + 1,
+                          label="bcc_799496")
+
+
+def bcc_cube(n: int, temperature: float = 300.0, sigma: float = 0.02, seed: int | None = None) -> System:
+    return thermal_system(BCC_TA_LIKE, (n, n, n), sigma, temperature,
+                          SEED_BASE + 100 + n if seed is None else seed, label=f"bcc_cube{n}")
+
+
+def multi_type_system(cells=(6, 6, 6), seed: int = SEED_BASE + 50, n_knots: int = 400) -> System:
+    """Two-species BCC alloy for the type-dependent code path: both species
+    use Johnson forms with different parameters; the cross pair function is
+    the average of the two pure ones (a synthetic choice)."""
+    pa = BCC_TA_LIKE
+    pb = dataclasses.replace(BCC_TA_LIKE, name="bcc_b", mass=95.95, re=2.75, E0=3.6,
+                             fe=1.2, A=0.7)
+    pos, box = bcc_lattice(*cells, pa.a)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pos = displace(pos, box, 0.03, rng)
+    types = (rng.random(pos.shape[0]) < 0.35).astype(np.int32)
+    masses = np.array([pa.mass, pb.mass])
+    vel = maxwell(pos.shape[0], masses[types], 400.0, rng)
+    Fa, fa, phia = johnson_knots(pa, n_knots)
+    Fb, fb, phib = johnson_knots(pb, n_knots)
+    phiab = Knots(phia.x0, phia.dx, 0.5 * (phia.y + phib.y), BC_CLAMPED, BC_NATURAL,
+                  0.5 * (phia.d_lo + phib.d_lo), 0.0)
+    pot = Potential(mass=masses, F=[Fa, Fb], f=[fa, fb], phi=[phia, phiab, phib],
+                    r_cut=pa.r_cut, skin=pa.skin)
+    return System(box=box, pos=pos, vel=vel, types=types, pot=pot, label="bcc_alloy")
