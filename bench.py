@@ -1,0 +1,331 @@
+"""Benchmark of the EAM timestep on GB300.
+
+Workload: the 799,496-atom BCC system (74x74x73 cells, Johnson-form EAM,
+2,000-knot cubic tables, r_cut 4.5 A, skin 0.3 A, sigma 0.02 A, 300 K),
+mixed precision (FP32 pair arithmetic; FP64 positions, velocities,
+integration and sums), dt = 2 fs, list rebuilt every 10 steps.
+
+One benchmark "step" is one pass of the whole hot path: 10 velocity-Verlet
+timesteps (a list rebuild: wrap, bin, sort, permute, list; ten density and
+force/integration passes) plus one energy/virial evaluation.  The metric is
+MD timesteps per second (higher is better).
+
+  value   device-timed throughput with the state resident in HBM (CUDA events
+          on the library's stream, K steps after W warm-up steps; the working
+          set, ~0.35 GB, is larger than L2, so no flush is needed)
+  e2e     the same metric through the C ABI with host buffers: per step
+          md_set_state from pinned host memory (positions + velocities),
+          md_step(10), md_energy (reads PE and KE back)
+
+--impl reference times the CPU oracle (the plain serial FP64 C reference)
+on a bounded sample of the same workload: one timestep per benchmark step.
+With torchrun (N > 1) every rank advances its own replica of the system
+(the single-system path does not shard across GPUs) and rank 0 reports the
+sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MD_STEPS_PER_BENCH_STEP = 10
+DT_FS = 2.0
+WORKLOAD = "bcc_799496_mixed"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self._proc = None
+        self._thread = None
+
+    def start(self):
+        try:
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self._proc = None
+            return
+        self._thread = threading.Thread(target=self._read, daemon=True)
+        self._thread.start()
+
+    def _read(self):
+        for line in self._proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self._proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self._proc.terminate()
+        try:
+            self._proc.wait(timeout=5)
+        except Exception:
+            self._proc.kill()
+        if self._thread:
+            self._thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(n_half: int):
+    """Algorithmic HBM bytes per atom-step of the mixed path (credited
+    independently of the implementation): FP64 positions and velocities read
+    and written (48 + 48), F' written and read (8), a half neighbour list read
+    by the density and the force pass (2 x 4 n_half), the rebuild amortised
+    over 10 steps ((4 n_half + 96) / 10).  Split per kernel: density = list +
+    F' write; force = positions + velocities + F' read + list."""
+    density = 4 * n_half + 4
+    force = 48 + 48 + 4 + 4 * n_half
+    rebuild = (4 * n_half + 96) / 10.0
+    return {"density": density, "force": force, "rebuild_amortised": rebuild,
+            "total": density + force + rebuild}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2405_07898_gb300 import binding, inputs as I
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    system = I.bcc_799496()
+    n = system.n
+    md = binding.MD(system, precision=args.precision, rebuild_every=10, use_graphs=True)
+    stream = md.stream
+
+    def bench_step():
+        md.step(MD_STEPS_PER_BENCH_STEP, DT_FS)
+
+    for _ in range(args.warmup):
+        bench_step()
+    md.sync()
+    launches0 = md.stats()["kernel_launches"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        bench_step()
+    e1.record(stream)
+    md.sync()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        ms_total = float(t.item())
+    launches = md.stats()["kernel_launches"] - launches0
+    ms_per_step = ms_total / args.steps
+    ts_per_s = world * args.steps * MD_STEPS_PER_BENCH_STEP / (ms_total * 1e-3)
+
+    # per-kernel durations with CUDA events (eager launches, same kernels)
+    prof = md.profile(args.profile_steps, DT_FS)
+    st = md.stats()
+    n_half = 13  # BCC, r_list = 4.8 A: 26 list entries per atom, 13 per pair direction
+    ab = algorithmic_bytes(n_half)
+    peak, peak_kind = peaks()
+    force_bytes = ab["force"] * n
+    achieved = force_bytes / (prof["force_ms"] * 1e-3) / 1e9
+    traffic = load_traffic()
+
+    # end-to-end through the C ABI with host buffers
+    pos_h = torch.from_numpy(system.pos.copy()).pin_memory()
+    vel_h = torch.from_numpy(system.vel.copy()).pin_memory()
+    md.set_state(pos_h, vel_h, 0)
+    md.step(MD_STEPS_PER_BENCH_STEP, DT_FS)
+    md.energy()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        md.set_state(pos_h, vel_h, 0)
+        md.step(MD_STEPS_PER_BENCH_STEP, DT_FS)
+        md.energy()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * args.e2e_steps * MD_STEPS_PER_BENCH_STEP / e2e_s
+    md.close()
+
+    if rank == 0:
+        cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu_baseline) else None
+        line = {
+            "metric": "timesteps/s at 800k atoms (mixed precision EAM MD)",
+            "value": ts_per_s,
+            "unit": "timesteps/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_per_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32+f64",
+            "data": "synthetic: seeded BCC lattice, Gaussian displacements, Maxwell velocities",
+            "config": {"workload": WORKLOAD, "atoms": n, "md_steps_per_step": MD_STEPS_PER_BENCH_STEP,
+                       "dt_fs": DT_FS, "rebuild_every": 10, "precision": args.precision,
+                       "list": "full Verlet list, r_list 4.8 A, 26 entries/atom",
+                       "l2": "working set ~0.35 GB > L2 (no flush needed)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "atom_steps_per_s": ts_per_s * n},
+            "e2e": {"value": e2e_value, "unit": "timesteps/s",
+                    "h2d_bytes_per_step": 2 * 3 * n * 8, "d2h_bytes_per_step": 16},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_force (force + integration)", "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_atom": ab["force"],
+                         "kernel_ms": prof["force_ms"]},
+            "kernels_ms": {"density": prof["density_ms"], "force": prof["force_ms"],
+                           "rebuild": prof["rebuild_ms"], "step": prof["step_ms"]},
+            "whole_step_hbm_frac": ab["total"] * n * ts_per_s / world / 1e9 / peak,
+            "clocks": clk,
+            "stats": {"rebuilds": st["rebuilds"], "max_neighbors": st["max_neighbors"]},
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def load_traffic():
+    """DRAM bytes per force launch from the committed ncu summary, if the
+    kernel has not changed since it was taken (else null)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as fh:
+            t = json.load(fh)
+        from paper_2405_07898_gb300 import build
+        import hashlib
+        src = open(os.path.join(build.CSRC, "kernels.cu"), "rb").read()
+        if t.get("kernels_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return t.get("force_dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def _oracle_sample(nsteps: int):
+    import oracle as O
+    from paper_2405_07898_gb300 import inputs as I
+
+    s = I.bcc_799496()
+    pot = O.Potential(s.pot)
+    sysm = O.System(pot, s.box, s.pos, s.vel, s.types)
+    t0 = time.perf_counter()
+    sysm.step(nsteps, DT_FS)
+    dt = time.perf_counter() - t0
+    return dt, s.n
+
+
+def cpu_baseline(args):
+    steps = args.cpu_steps
+    dt, n = _oracle_sample(steps)
+    return {"value": steps / dt, "unit": "timesteps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} timesteps of the 799,496-atom system (serial FP64 C oracle, "
+                      f"list rebuilt every 10 steps), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2405_07898_gb300 import inputs as I
+
+    s = I.bcc_799496()
+    pot = O.Potential(s.pot)
+    sysm = O.System(pot, s.box, s.pos, s.vel, s.types)
+    for _ in range(args.warmup):
+        sysm.step(1, DT_FS)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sysm.step(1, DT_FS)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {
+        "impl": "reference",
+        "metric": "timesteps/s at 800k atoms (mixed precision EAM MD)",
+        "value": value, "unit": "timesteps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: seeded BCC lattice, Gaussian displacements, Maxwell velocities",
+        "config": {"workload": WORKLOAD, "atoms": s.n, "md_steps_per_step": 1, "dt_fs": DT_FS,
+                   "rebuild_every": 10},
+        "cpu_baseline": {"value": value, "unit": "timesteps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} timesteps after {args.warmup} warm-up, serial FP64 C oracle"},
+        "e2e": {"value": value, "unit": "timesteps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * eammd.h -- C ABI of the GB300 (sm_103a) Embedded-Atom-Method molecular
+ * dynamics library.
+ *
+ * The library advances periodic systems of atoms under an EAM potential
+ * (arXiv 2405.07898, Section "Computational Molecular Dynamics"):
+ *   density   rho_i = sum_{j != i, r_ij < r_cut} f_{t_j}(r_ij)               (Eq. 2)
+ *   energy    U = 1/2 sum_{i != j} phi_{t_i t_j}(r_ij) + sum_i F_{t_i}(rho_i) (Eq. 3)
+ *   force     F_i = sum_j [phi'(r) + F'_i f'_{t_j}(r) + F'_j f'_{t_i}(r)] (x_j - x_i)/r  (Eq. 4)
+ *   motion    velocity Verlet, whose half-step velocities are the leap-frog
+ *             velocities of Eq. 5,
+ * with a cell-binned Verlet neighbour list of radius r_cut + skin (Section
+ * "Neighbor list": the squared distance is compared with the squared
+ * radius) under periodic boundaries (Section "Periodic Boundary Conditions").
+ *
+ * Conventions shared by every entry point:
+ *   - Units are metal units: Angstrom, eV, amu, fs.
+ *   - Host arrays are caller-owned; the library copies what it needs and
+ *     never keeps a host pointer past the call.  Per-atom arrays are in the
+ *     caller's original atom order, xyz interleaved (n*3 doubles).
+ *   - Every call returns an md_status; nothing throws across the ABI.
+ *     md_last_error() gives a human-readable message for the last failure.
+ *   - Device work is queued on the context's CUDA stream.  md_step returns
+ *     once its work is queued; errors raised on the device (neighbour-list
+ *     overflow, non-finite forces) are sticky and reported by the next call
+ *     that synchronises (md_sync, md_energy, md_forces, md_virial,
+ *     md_get_state, md_neighbors, md_cells, md_stats).
+ *   - A context is used from one host thread at a time.
+ */
+#ifndef EAMMD_H
+#define EAMMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct md_ctx md_ctx;
+
+typedef enum {
+    MD_OK = 0,
+    MD_ERR_ARG = -1,          /* invalid argument (null pointer, n < 0, bad table, ...) */
+    MD_ERR_BOX = -2,          /* some box edge is shorter than 3 (r_cut + skin) */
+    MD_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+    MD_ERR_OOM = -4,          /* device allocation failed */
+    MD_ERR_NONFINITE = -5,    /* a force or an input coordinate was not finite */
+    MD_ERR_TIMEOUT = -6,      /* a bounded device wait gave up */
+    MD_ERR_LIST_OVERFLOW = -7,/* an atom had more neighbours than the list capacity */
+    MD_ERR_CAPACITY = -8      /* a size is beyond a compiled-in or configured maximum */
+} md_status;
+
+/* Uniform-knot cubic spline: knots x0 + k*dx, k = 0..n-1, values y[k].
+ * The library builds the C2 interpolating cubic.  bc_lo / bc_hi select
+ * the end condition: 0 = natural (zero second derivative), 1 = clamped
+ * (first derivative d_lo / d_hi).  Outside [x0, x0+(n-1)dx] the spline
+ * continues along its end tangent.  n >= 2, dx > 0. */
+typedef struct {
+    int32_t n;
+    double x0, dx;
+    const double *y;
+    int32_t bc_lo, bc_hi;
+    double d_lo, d_hi;
+} md_spline;
+
+/* EAM potential over ntypes atom types (1 <= ntypes <= 8), the
+ * type-dependent splines of Section "Computational Molecular Dynamics":
+ *   mass[t]  amu;
+ *   F[t]     embedding energy of an atom of type t, a function of density;
+ *   f[t]     density contributed by an atom of type t at distance r;
+ *   phi[q]   pair energy of types (a <= b), q = a*ntypes - a*(a-1)/2 + (b-a).
+ * The f and phi tables must start at r <= 0 and extend to at least r_cut.
+ * The potential vanishes for r >= r_cut; the list radius is r_cut + skin. */
+typedef struct {
+    int32_t ntypes;
+    const double *mass;
+    const md_spline *F;
+    const md_spline *f;
+    const md_spline *phi;
+    double r_cut, skin;
+} md_potential;
+
+enum { MD_PRECISION_FP64 = 0, MD_PRECISION_MIXED = 1 };
+
+/* Options.  Fill with md_options_default() and change what you need.
+ *   precision        MD_PRECISION_FP64: all arithmetic in FP64.
+ *                    MD_PRECISION_MIXED: pair distance, spline, density and
+ *                    force arithmetic in FP32 on cell-relative coordinates;
+ *                    positions, velocities, integration and the energy /
+ *                    virial sums over atoms in FP64.
+ *   rebuild_every    rebuild the neighbour list after this many steps (10),
+ *                    or sooner when an atom has moved more than skin/2.
+ *   list_capacity    neighbours per atom the list can hold; 0 = sized from
+ *                    the initial configuration.
+ *   cuda_stream      cudaStream_t to queue work on; NULL = the library
+ *                    creates its own stream.
+ *   alloc / free     device allocator callbacks (e.g. a framework caching
+ *                    allocator); NULL = cudaMalloc / cudaFree.  alloc must
+ *                    return 256-byte aligned device memory or NULL.
+ *   use_graphs       1 = replay the step sequence as CUDA graphs with a
+ *                    device-side conditional node for the list rebuild;
+ *                    0 = launch kernels one by one (same kernels, same results).
+ *   block_size       threads per block of the per-atom kernels (0 = 256). */
+typedef struct {
+    int32_t precision;
+    int32_t rebuild_every;
+    int32_t list_capacity;
+    int32_t use_graphs;
+    int32_t block_size;
+    int32_t reserved0;
+    void *cuda_stream;
+    void *(*alloc)(size_t bytes, void *alloc_ctx);
+    void (*free)(void *ptr, void *alloc_ctx);
+    void *alloc_ctx;
+} md_options;
+
+void md_options_default(md_options *opt);
+
+/* Create a system of n atoms in the periodic box [0,box[0]) x [0,box[1]) x
+ * [0,box[2]).  pos: n*3 Angstrom (any image; wrapped on entry);
+ * vel: n*3 Angstrom/fs or NULL for zero; types: n values in [0, ntypes).
+ * Builds the tables, bins the atoms, builds the list and evaluates the
+ * forces, energies and virial of the initial state.  Synchronises.
+ * Errors: MD_ERR_ARG, MD_ERR_BOX, MD_ERR_NONFINITE, MD_ERR_OOM, MD_ERR_CUDA,
+ * MD_ERR_CAPACITY (n >= 2^27). */
+md_status md_create(const double box[3], int64_t n, const double *pos, const double *vel,
+                    const int32_t *types, const md_potential *pot, const md_options *opt,
+                    md_ctx **out);
+
+/* Advance nsteps velocity-Verlet steps of dt fs: per step kick (dt/2),
+ * drift (dt), rebuild the list if due, density and force, kick (dt/2).
+ * Energies and the virial are evaluated at the last step.  Asynchronous:
+ * returns once the work is queued on the context's stream. */
+md_status md_step(md_ctx *ctx, int64_t nsteps, double dt);
+
+/* Wait for queued work and report sticky device errors. */
+md_status md_sync(md_ctx *ctx);
+
+/* Potential (Eq. 3) and kinetic energy of the current state, eV. */
+md_status md_energy(md_ctx *ctx, double *pe, double *ke);
+
+/* Forces of the current state into f (n*3, eV/Angstrom, original order). */
+md_status md_forces(md_ctx *ctx, double *f);
+
+/* Virial W_ab = -1/2 sum_i sum_{j != i} s_ij d_a d_b / r_ij (d = x_j - x_i,
+ * s_ij the scalar of Eq. 4), ordered xx, yy, zz, xy, xz, yz, eV.  The
+ * pressure is (2 KE + W_xx + W_yy + W_zz) / (3 V). */
+md_status md_virial(md_ctx *ctx, double w[6]);
+
+/* Current positions (wrapped at the last list build, then advanced),
+ * velocities (at the integer step) and the step counter; any pointer may
+ * be NULL. */
+md_status md_get_state(md_ctx *ctx, double *pos, double *vel, int64_t *step);
+
+/* Replace positions and velocities (original order), rebuild the list and
+ * re-evaluate forces and energies.  vel may be NULL for zero. */
+md_status md_set_state(md_ctx *ctx, const double *pos, const double *vel, int64_t step);
+
+/* Neighbour list of the last build in original atom ids, CSR:
+ * offsets[n+1] and js[offsets[n]].  js is written only if offsets[n] <= cap;
+ * the needed size is always returned in offsets[n]. */
+md_status md_neighbors(md_ctx *ctx, int64_t *offsets, int32_t *js, int64_t cap);
+
+/* Cell bins of the last build: ncell[3] cells per axis, cell_start[ncells+1],
+ * cell_atoms[n] (original ids, ascending within each cell).  Any array may
+ * be NULL to query ncell only. */
+md_status md_cells(md_ctx *ctx, int32_t ncell[3], int32_t *cell_start, int32_t *cell_atoms);
+
+/* Counters of the run so far. */
+typedef struct {
+    int64_t steps;           /* velocity-Verlet steps taken */
+    int64_t rebuilds;        /* neighbour-list builds after md_create */
+    int32_t max_neighbors;   /* largest list length at the last build */
+    int32_t list_capacity;   /* list slots per atom */
+    int64_t table_out_of_range; /* embedding lookups beyond the F table */
+    int64_t kernel_launches; /* kernels queued by this context so far */
+} md_stats_t;
+
+md_status md_stats(md_ctx *ctx, md_stats_t *out);
+
+/* Kernel timing: runs nsteps ordinary steps of dt fs (the state advances as
+ * with md_step) with kernels launched one by one, each density launch, force
+ * launch and list rebuild bracketed by CUDA events on the context's stream,
+ * and returns their average durations in milliseconds.  Synchronises. */
+typedef struct {
+    double density_ms;       /* average density (Eq. 2) kernel */
+    double force_ms;         /* average force + integration (Eqs. 4, 5) kernel */
+    double rebuild_ms;       /* average full list rebuild (8 kernels) */
+    double step_ms;          /* average wall time of one step on the stream */
+    int64_t density_launches, force_launches, rebuilds;
+} md_profile_t;
+
+md_status md_profile(md_ctx *ctx, int64_t nsteps, double dt, md_profile_t *out);
+
+/* Message for the last failed call on ctx (or of md_create when ctx is NULL). */
+const char *md_last_error(const md_ctx *ctx);
+
+/* Free everything the context owns.  Safe on NULL. */
+void md_destroy(md_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EAMMD_H */

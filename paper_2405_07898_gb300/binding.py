@@ -1,0 +1,304 @@
+"""ctypes binding of the C ABI in include/eammd.h (argument marshalling only;
+every step of the method runs in the CUDA library).
+
+PyTorch supplies device memory (its caching allocator, through the
+md_options alloc/free callbacks) and the CUDA stream (its current stream).
+The library must be built (`paper_2405_07898_gb300.build.build()`); loading
+fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_lp = C.POINTER(C.c_int64)
+
+MD_OK = 0
+STATUS = {0: "MD_OK", -1: "MD_ERR_ARG", -2: "MD_ERR_BOX", -3: "MD_ERR_CUDA", -4: "MD_ERR_OOM",
+          -5: "MD_ERR_NONFINITE", -6: "MD_ERR_TIMEOUT", -7: "MD_ERR_LIST_OVERFLOW",
+          -8: "MD_ERR_CAPACITY"}
+PRECISION = {"fp64": 0, "mixed": 1}
+
+# every entry point declared in include/eammd.h
+EXPORTS = ("md_options_default", "md_create", "md_step", "md_sync", "md_energy", "md_forces",
+           "md_virial", "md_get_state", "md_set_state", "md_neighbors", "md_cells", "md_stats",
+           "md_profile", "md_last_error", "md_destroy")
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Spline(C.Structure):
+    _fields_ = [("n", C.c_int32), ("x0", C.c_double), ("dx", C.c_double), ("y", _dp),
+                ("bc_lo", C.c_int32), ("bc_hi", C.c_int32), ("d_lo", C.c_double),
+                ("d_hi", C.c_double)]
+
+
+class PotentialC(C.Structure):
+    _fields_ = [("ntypes", C.c_int32), ("mass", _dp), ("F", C.POINTER(Spline)),
+                ("f", C.POINTER(Spline)), ("phi", C.POINTER(Spline)), ("r_cut", C.c_double),
+                ("skin", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("rebuild_every", C.c_int32),
+                ("list_capacity", C.c_int32), ("use_graphs", C.c_int32),
+                ("block_size", C.c_int32), ("reserved0", C.c_int32),
+                ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("rebuilds", C.c_int64), ("max_neighbors", C.c_int32),
+                ("list_capacity", C.c_int32), ("table_out_of_range", C.c_int64),
+                ("kernel_launches", C.c_int64)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("density_ms", C.c_double), ("force_ms", C.c_double), ("rebuild_ms", C.c_double),
+                ("step_ms", C.c_double), ("density_launches", C.c_int64),
+                ("force_launches", C.c_int64), ("rebuilds", C.c_int64)]
+
+
+class MDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libeammd.so (building it first if asked and needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing")
+    L = C.CDLL(path)
+    L.md_options_default.argtypes = [C.POINTER(Options)]
+    L.md_options_default.restype = None
+    L.md_create.argtypes = [_dp, C.c_int64, _dp, _dp, _ip, C.POINTER(PotentialC), C.POINTER(Options),
+                            C.POINTER(C.c_void_p)]
+    L.md_create.restype = C.c_int
+    L.md_step.argtypes = [C.c_void_p, C.c_int64, C.c_double]
+    L.md_step.restype = C.c_int
+    L.md_sync.argtypes = [C.c_void_p]
+    L.md_sync.restype = C.c_int
+    L.md_energy.argtypes = [C.c_void_p, _dp, _dp]
+    L.md_energy.restype = C.c_int
+    L.md_forces.argtypes = [C.c_void_p, _dp]
+    L.md_forces.restype = C.c_int
+    L.md_virial.argtypes = [C.c_void_p, _dp]
+    L.md_virial.restype = C.c_int
+    L.md_get_state.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, _lp]
+    L.md_get_state.restype = C.c_int
+    L.md_set_state.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
+    L.md_set_state.restype = C.c_int
+    L.md_neighbors.argtypes = [C.c_void_p, _lp, _ip, C.c_int64]
+    L.md_neighbors.restype = C.c_int
+    L.md_cells.argtypes = [C.c_void_p, _ip, _ip, _ip]
+    L.md_cells.restype = C.c_int
+    L.md_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
+    L.md_stats.restype = C.c_int
+    L.md_profile.argtypes = [C.c_void_p, C.c_int64, C.c_double, C.POINTER(Profile)]
+    L.md_profile.restype = C.c_int
+    L.md_last_error.argtypes = [C.c_void_p]
+    L.md_last_error.restype = C.c_char_p
+    L.md_destroy.argtypes = [C.c_void_p]
+    L.md_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    """Host pointer of a numpy array or a (pinned) CPU torch tensor."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _torch_allocator(stream):
+    import torch
+
+    def alloc(nbytes, _ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=stream)
+        except Exception:  # out of memory -> NULL, the library reports MD_ERR_OOM
+            return None
+
+    def free(ptr, _ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return ALLOC_FN(alloc), FREE_FN(free)
+
+
+class MD:
+    """One periodic EAM system on the GPU (the md_ctx of include/eammd.h).
+
+    `system` is an `inputs.System`.  precision: "mixed" or "fp64".
+    With use_torch=True (default when CUDA is available to torch) device
+    memory comes from torch's caching allocator and work is queued on a
+    torch stream owned by this object (`self.stream`)."""
+
+    def __init__(self, system, precision: str = "mixed", rebuild_every: int = 10,
+                 list_capacity: int = 0, use_graphs: bool = True, block_size: int = 256,
+                 use_torch: bool | None = None):
+        L = load()
+        self._L = L
+        self.n = int(system.n)
+        self.system = system
+        opt = Options()
+        L.md_options_default(C.byref(opt))
+        opt.precision = PRECISION[precision]
+        opt.rebuild_every = rebuild_every
+        opt.list_capacity = list_capacity
+        opt.use_graphs = 1 if use_graphs else 0
+        opt.block_size = block_size
+        self._keep = []
+        if use_torch is None:
+            try:
+                import torch
+                use_torch = torch.cuda.is_available()
+            except Exception:
+                use_torch = False
+        if use_torch:
+            import torch
+            torch.cuda.init()
+            self.stream = torch.cuda.Stream()
+            a, f = _torch_allocator(self.stream)
+            self._keep += [a, f]
+            opt.alloc, opt.free = a, f
+            opt.cuda_stream = C.c_void_p(self.stream.cuda_stream)
+        pot = system.pot
+
+        def splines(ks):
+            arr = (Spline * len(ks))()
+            for q, k in enumerate(ks):
+                y = _f64(k.y)
+                self._keep.append(y)
+                arr[q] = Spline(k.n, k.x0, k.dx, _d(y), k.bc_lo, k.bc_hi, k.d_lo, k.d_hi)
+            return arr
+
+        mass = _f64(pot.mass)
+        self._keep.append(mass)
+        pc = PotentialC(pot.ntypes, _d(mass), splines(pot.F), splines(pot.f), splines(pot.phi),
+                        pot.r_cut, pot.skin)
+        box = _f64(system.box)
+        pos = _f64(system.pos)
+        vel = _f64(system.vel) if system.vel is not None else None
+        types = np.ascontiguousarray(system.types, dtype=np.int32)
+        h = C.c_void_p()
+        rc = L.md_create(_d(box), self.n, _d(pos), _d(vel) if vel is not None else None,
+                         types.ctypes.data_as(_ip), C.byref(pc), C.byref(opt), C.byref(h))
+        if rc != MD_OK:
+            raise MDError(rc, L.md_last_error(None).decode())
+        self.h = h
+        self.box = box
+
+    def _check(self, rc):
+        if rc != MD_OK:
+            raise MDError(rc, self._L.md_last_error(self.h).decode())
+
+    def step(self, nsteps: int, dt: float):
+        self._check(self._L.md_step(self.h, int(nsteps), float(dt)))
+
+    def sync(self):
+        self._check(self._L.md_sync(self.h))
+
+    def energy(self):
+        pe, ke = C.c_double(), C.c_double()
+        self._check(self._L.md_energy(self.h, C.byref(pe), C.byref(ke)))
+        return pe.value, ke.value
+
+    def virial(self):
+        w = np.zeros(6)
+        self._check(self._L.md_virial(self.h, _d(w)))
+        return w
+
+    def forces(self, out=None):
+        out = np.zeros((self.n, 3)) if out is None else out
+        self._check(self._L.md_forces(self.h, _d(out) if isinstance(out, np.ndarray) else _ptr(out)))
+        return out
+
+    def get_state(self, pos=None, vel=None):
+        pos = np.zeros((self.n, 3)) if pos is None else pos
+        vel = np.zeros((self.n, 3)) if vel is None else vel
+        st = C.c_int64()
+        self._check(self._L.md_get_state(self.h, _ptr(pos), _ptr(vel), C.byref(st)))
+        return pos, vel, st.value
+
+    def set_state(self, pos, vel=None, step: int = 0):
+        if isinstance(pos, np.ndarray):
+            pos = _f64(pos)
+        if isinstance(vel, np.ndarray):
+            vel = _f64(vel)
+        self._check(self._L.md_set_state(self.h, _ptr(pos), _ptr(vel), int(step)))
+
+    def neighbors(self):
+        off = np.zeros(self.n + 1, dtype=np.int64)
+        self._check(self._L.md_neighbors(self.h, off.ctypes.data_as(_lp), None, 0))
+        js = np.zeros(max(int(off[-1]), 1), dtype=np.int32)
+        self._check(self._L.md_neighbors(self.h, off.ctypes.data_as(_lp), js.ctypes.data_as(_ip),
+                                         js.shape[0]))
+        return off, js[: int(off[-1])]
+
+    def cells(self):
+        nc = np.zeros(3, dtype=np.int32)
+        self._check(self._L.md_cells(self.h, nc.ctypes.data_as(_ip), None, None))
+        ncells = int(np.prod(nc.astype(np.int64)))
+        start = np.zeros(ncells + 1, dtype=np.int32)
+        atoms = np.zeros(max(self.n, 1), dtype=np.int32)
+        self._check(self._L.md_cells(self.h, nc.ctypes.data_as(_ip), start.ctypes.data_as(_ip),
+                                     atoms.ctypes.data_as(_ip)))
+        return nc, start, atoms[: self.n]
+
+    def stats(self):
+        s = Stats()
+        self._check(self._L.md_stats(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def profile(self, nsteps: int, dt: float):
+        """Average kernel durations (ms) over nsteps eagerly launched steps."""
+        p = Profile()
+        self._check(self._L.md_profile(self.h, int(nsteps), float(dt), C.byref(p)))
+        return {k: getattr(p, k) for k, _ in Profile._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.md_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,925 @@
+// md_capi.cu -- host runtime behind the C ABI of include/eammd.h: spline
+// tables, device memory, the step schedule (eager launches or CUDA graphs
+// whose list rebuild sits in a device-side conditional node), and the
+// marshalling of states between the caller's order and the sorted order.
+#include "eammd.h"
+#include "md_internal.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace eammd;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// --------------------------------------------------------------------------
+// Spline tables.  The C2 cubic through uniform knots is parametrised by its
+// knot slopes m_k: continuity of the second derivative at interior knots gives
+//   m_{k-1} + 4 m_k + m_{k+1} = 3 (y_{k+1} - y_{k-1}) / h,
+// a natural end gives 2 m_0 + m_1 = 3 (y_1 - y_0) / h (and its mirror), a
+// clamped end fixes the slope.  Each interval is the Hermite cubic through
+// (y_k, m_k) and (y_{k+1}, m_{k+1}).
+bool hermite_coefficients(const md_spline &s, std::vector<double> &rows)
+{
+    const int n = s.n;
+    const double h = s.dx;
+    const double *y = s.y;
+    std::vector<double> lo(n, 0.0), di(n, 0.0), up(n, 0.0), rhs(n, 0.0), m(n, 0.0);
+    if (s.bc_lo == 1) {
+        di[0] = 1.0; rhs[0] = s.d_lo;
+    } else {
+        di[0] = 2.0; up[0] = 1.0; rhs[0] = 3.0 * (y[1] - y[0]) / h;
+    }
+    for (int k = 1; k < n - 1; ++k) {
+        lo[k] = 1.0; di[k] = 4.0; up[k] = 1.0;
+        rhs[k] = 3.0 * (y[k + 1] - y[k - 1]) / h;
+    }
+    if (s.bc_hi == 1) {
+        di[n - 1] = 1.0; rhs[n - 1] = s.d_hi;
+    } else {
+        lo[n - 1] = 1.0; di[n - 1] = 2.0; rhs[n - 1] = 3.0 * (y[n - 1] - y[n - 2]) / h;
+    }
+    // tridiagonal solve (forward sweep, back substitution)
+    for (int k = 1; k < n; ++k) {
+        double w = lo[k] / di[k - 1];
+        di[k] -= w * up[k - 1];
+        rhs[k] -= w * rhs[k - 1];
+    }
+    m[n - 1] = rhs[n - 1] / di[n - 1];
+    for (int k = n - 2; k >= 0; --k) m[k] = (rhs[k] - up[k] * m[k + 1]) / di[k];
+    for (int k = 0; k < n - 1; ++k) {
+        double dy = (y[k + 1] - y[k]) / h;
+        rows.push_back(y[k]);
+        rows.push_back(m[k]);
+        rows.push_back((3.0 * dy - 2.0 * m[k] - m[k + 1]) / h);
+        rows.push_back((m[k] + m[k + 1] - 2.0 * dy) / (h * h));
+    }
+    for (double v : m)
+        if (!std::isfinite(v)) return false;
+    return true;
+}
+
+template <class R>
+SplineDesc<R> make_desc(const md_spline &s, int offset, const double *row_last, const double *row0)
+{
+    SplineDesc<R> d;
+    d.offset = offset;
+    d.nint = s.n - 1;
+    d.x0 = (R)s.x0;
+    d.inv_h = (R)(1.0 / s.dx);
+    d.h_hi = (R)s.dx;
+    d.h_lo = (R)(s.dx - (double)d.h_hi);
+    double x_end = s.x0 + (double)(s.n - 1) * s.dx;
+    d.x_end = (R)x_end;
+    d.y_lo = (R)row0[0];
+    d.s_lo = (R)row0[1];
+    double t = s.dx;
+    d.y_end = (R)(row_last[0] + t * (row_last[1] + t * (row_last[2] + t * row_last[3])));
+    d.s_end = (R)(row_last[1] + t * (2.0 * row_last[2] + 3.0 * t * row_last[3]));
+    return d;
+}
+
+bool spline_ok(const md_spline &s)
+{
+    if (s.n < 2 || !(s.dx > 0.0) || !std::isfinite(s.dx) || !std::isfinite(s.x0) || !s.y) return false;
+    for (int k = 0; k < s.n; ++k)
+        if (!std::isfinite(s.y[k])) return false;
+    if (s.bc_lo == 1 && !std::isfinite(s.d_lo)) return false;
+    if (s.bc_hi == 1 && !std::isfinite(s.d_hi)) return false;
+    return true;
+}
+
+struct GraphEntry {
+    int kind;     // 0 = middle steps, 1 = closing step
+    int nsteps;
+    double dt;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct md_ctx {
+    int precision = MD_PRECISION_MIXED;
+    int64_t n = 0;
+    int ntypes = 1;
+    double box[3] = {0, 0, 0};
+    md_options opt{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr, body_stream = nullptr;
+    Geom G{};
+    Launch L{};
+    double mass[kMaxTypes] = {0};
+    std::vector<void *> allocs;
+    Bufs<float> Bf{};
+    Bufs<double> Bd{};
+    DevState *st = nullptr;
+    DevState *st_host = nullptr;  // pinned
+    double *stage = nullptr;      // 9 n doubles: AoS pos, vel, force
+    int *types_orig = nullptr;
+    std::vector<GraphEntry> graphs;
+    long long fixed_launches = 0;
+    long long rebuilds_at_create = 0;
+    int64_t host_steps = 0;       // step counter when n == 0
+    std::string err;
+
+    md_status fail(md_status s, const std::string &m)
+    {
+        err = m;
+        return s;
+    }
+};
+
+namespace {
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            return ctx->fail(e_ == cudaErrorMemoryAllocation ? MD_ERR_OOM : MD_ERR_CUDA,           \
+                             std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+        }                                                                                          \
+    } while (0)
+
+void *dalloc(md_ctx *ctx, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~size_t(255);
+    void *p = nullptr;
+    if (ctx->opt.alloc) {
+        p = ctx->opt.alloc(bytes, ctx->opt.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) ctx->allocs.push_back(p);
+    return p;
+}
+
+void dfree_all(md_ctx *ctx)
+{
+    for (void *p : ctx->allocs) {
+        if (ctx->opt.free) ctx->opt.free(p, ctx->opt.alloc_ctx);
+        else cudaFree(p);
+    }
+    ctx->allocs.clear();
+}
+
+template <class T>
+bool alloc_n(md_ctx *ctx, T *&p, size_t count)
+{
+    p = (T *)dalloc(ctx, count * sizeof(T));
+    return p != nullptr;
+}
+
+template <class R>
+Bufs<R> &bufs(md_ctx *ctx);
+template <>
+Bufs<float> &bufs<float>(md_ctx *ctx) { return ctx->Bf; }
+template <>
+Bufs<double> &bufs<double>(md_ctx *ctx) { return ctx->Bd; }
+
+template <class R>
+bool alloc_buffers(md_ctx *ctx, const std::vector<double> &rows, const Tables<R> &tables)
+{
+    using R4 = typename V4<R>::T;
+    Bufs<R> &B = bufs<R>(ctx);
+    const size_t n = (size_t)std::max<int64_t>(ctx->n, 1);
+    const Geom &G = ctx->G;
+    bool ok = true;
+    for (int s = 0; s < 2; ++s)
+        for (int a = 0; a < 3; ++a) {
+            ok = ok && alloc_n(ctx, B.xr[s][a], n);
+            ok = ok && alloc_n(ctx, B.v[s][a], n);
+        }
+    for (int a = 0; a < 3; ++a) {
+        ok = ok && alloc_n(ctx, B.d[a], n);
+        ok = ok && alloc_n(ctx, B.xw[a], n);
+        ok = ok && alloc_n(ctx, B.uref[a], n);
+        ok = ok && alloc_n(ctx, B.fcache[a], n);
+        ok = ok && alloc_n(ctx, B.center[a], (size_t)G.ncell[a]);
+    }
+    for (int s = 0; s < 2; ++s) {
+        ok = ok && alloc_n(ctx, B.id[s], n);
+        ok = ok && alloc_n(ctx, B.type[s], n);
+        ok = ok && alloc_n(ctx, B.shadow[s], n);
+    }
+    ok = ok && alloc_n(ctx, B.Fp, n);
+    ok = ok && alloc_n(ctx, B.cell, n);
+    ok = ok && alloc_n(ctx, B.cell_old, n);
+    ok = ok && alloc_n(ctx, B.slot, n);
+    ok = ok && alloc_n(ctx, B.cell_atoms, n);
+    ok = ok && alloc_n(ctx, B.nnb, n);
+    ok = ok && alloc_n(ctx, B.count, (size_t)G.ncells + 1);
+    ok = ok && alloc_n(ctx, B.cell_start, (size_t)G.ncells + 1);
+    ok = ok && alloc_n(ctx, B.block_sums, (size_t)(G.ncells + kScanBlock - 1) / kScanBlock + 1);
+    ok = ok && alloc_n(ctx, B.partials, (size_t)kEnergySlots * std::max(ctx->L.nblocks, 1));
+    ok = ok && alloc_n(ctx, B.list, (size_t)ctx->L.cap * ctx->L.ld);
+    R4 *coef = nullptr;
+    Tables<R> *tab = nullptr;
+    ok = ok && alloc_n(ctx, coef, rows.size() / 4);
+    ok = ok && alloc_n(ctx, tab, 1);
+    if (!ok) return false;
+    B.coef = coef;
+    B.tables = tab;
+    B.st = ctx->st;
+    std::vector<R4> rr(rows.size() / 4);
+    for (size_t k = 0; k < rr.size(); ++k) {
+        R *dst = reinterpret_cast<R *>(&rr[k]);
+        for (int c = 0; c < 4; ++c) dst[c] = (R)rows[4 * k + c];
+    }
+    if (cudaMemcpy(coef, rr.data(), rr.size() * sizeof(R4), cudaMemcpyHostToDevice) != cudaSuccess) return false;
+    if (cudaMemcpy(tab, &tables, sizeof(Tables<R>), cudaMemcpyHostToDevice) != cudaSuccess) return false;
+    for (int a = 0; a < 3; ++a) {
+        std::vector<double> c(G.ncell[a]);
+        for (int k = 0; k < G.ncell[a]; ++k) c[k] = ((double)k + 0.5) * G.h[a];
+        if (cudaMemcpy(B.center[a], c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+            return false;
+    }
+    if (cudaMemset(B.count, 0, sizeof(int) * ((size_t)G.ncells + 1)) != cudaSuccess) return false;
+    if (cudaMemset(B.nnb, 0, sizeof(int) * n) != cudaSuccess) return false;
+    for (int a = 0; a < 3; ++a)
+        if (cudaMemset(B.fcache[a], 0, sizeof(R) * n) != cudaSuccess) return false;
+    return true;
+}
+
+void drop_graphs(md_ctx *ctx)
+{
+    for (auto &g : ctx->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+    }
+    ctx->graphs.clear();
+}
+
+template <class R>
+bool grow_list(md_ctx *ctx, int cap)
+{
+    Bufs<R> &B = bufs<R>(ctx);
+    drop_graphs(ctx);  // captured kernels hold the old list pointer
+    uint32_t *nl = nullptr;
+    if (!alloc_n(ctx, nl, (size_t)cap * ctx->L.ld)) return false;
+    // the old block stays owned by the context until md_destroy
+    B.list = nl;
+    ctx->L.cap = cap;
+    return true;
+}
+
+md_status read_state(md_ctx *ctx)
+{
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(ctx->st_host, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    return MD_OK;
+}
+
+md_status check_device_errors(md_ctx *ctx)
+{
+    md_status rc = read_state(ctx);
+    if (rc != MD_OK) return rc;
+    unsigned int e = ctx->st_host->error;
+    if (e & ERR_LIST_OVERFLOW)
+        return ctx->fail(MD_ERR_LIST_OVERFLOW, "an atom had more neighbours (" +
+                                                   std::to_string(ctx->st_host->max_nnb) +
+                                                   ") than the list capacity (" + std::to_string(ctx->L.cap) + ")");
+    if (e & ERR_NONFINITE) return ctx->fail(MD_ERR_NONFINITE, "non-finite position or force");
+    if (e & ERR_TIMEOUT) return ctx->fail(MD_ERR_TIMEOUT, "a bounded device wait gave up");
+    return MD_OK;
+}
+
+// Rebuild + density + force (no integration) + reduction at the current
+// positions: the state after md_create / md_set_state.
+template <class R>
+md_status measure(md_ctx *ctx)
+{
+    const Bufs<R> &B = bufs<R>(ctx);
+    Launch L = ctx->L;
+    L.use_cond = 0;
+    L.cond = 0;
+    ctx->fixed_launches += launch_rebuild<R>(B, ctx->G, L);
+    ctx->fixed_launches += launch_density<R>(B, ctx->G, L, true);
+    ctx->fixed_launches += launch_force<R>(B, ctx->G, L, MODE_MEASURE, true);
+    ctx->fixed_launches += launch_reduce<R>(B, L);
+    CK(cudaGetLastError());
+    return MD_OK;
+}
+
+// Upload a state in the caller's order and evaluate it.  When the list
+// overflows and the capacity was not fixed by the caller, grow and retry.
+template <class R>
+md_status load_and_measure(md_ctx *ctx, const double *pos, const double *vel, int64_t step)
+{
+    const Bufs<R> &B0 = bufs<R>(ctx);
+    const size_t n = (size_t)ctx->n;
+    // the permutation restarts from the caller's order in buffer set 0
+    DevState h{};
+    h.step = step;
+    h.need_rebuild = 1;
+    h.set = 0;
+    h.sp = 0;
+    CK(cudaMemcpyAsync(ctx->st, &h, sizeof(DevState), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->stage, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if (vel) CK(cudaMemcpyAsync(ctx->stage + 3 * n, vel, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    Launch L = ctx->L;
+    ctx->fixed_launches += launch_load_state<R>(B0, L, ctx->stage, vel ? ctx->stage + 3 * n : nullptr, ctx->types_orig);
+    CK(cudaGetLastError());
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        md_status rc = measure<R>(ctx);
+        if (rc != MD_OK) return rc;
+        rc = read_state(ctx);
+        if (rc != MD_OK) return rc;
+        const DevState &hs = *ctx->st_host;
+        if ((hs.error & ERR_LIST_OVERFLOW) && ctx->opt.list_capacity <= 0) {
+            int cap = ((hs.max_nnb + hs.max_nnb / 8 + 8) + 3) & ~3;
+            if (!grow_list<R>(ctx, cap)) return ctx->fail(MD_ERR_OOM, "cannot grow the neighbour list");
+            // the state is already sorted; rebuild from it with the larger capacity
+            DevState again = hs;
+            again.error &= ~ERR_LIST_OVERFLOW;
+            again.need_rebuild = 1;
+            again.rebuilds = 0;
+            CK(cudaMemcpy(ctx->st, &again, sizeof(DevState), cudaMemcpyHostToDevice));
+            continue;
+        }
+        break;
+    }
+    md_status rc = check_device_errors(ctx);
+    if (rc != MD_OK) return rc;
+    // rebuilds are counted from here on
+    DevState hs = *ctx->st_host;
+    ctx->rebuilds_at_create = hs.rebuilds;
+    return MD_OK;
+}
+
+template <class R>
+void enqueue_step(md_ctx *ctx, const Launch &L, bool last)
+{
+    const Bufs<R> &B = bufs<R>(ctx);
+    launch_decide<R>(B, L);
+    if (L.use_cond) {
+        // the rebuild kernels are captured into the conditional node body by the caller
+    } else {
+        launch_rebuild<R>(B, ctx->G, L);
+    }
+    launch_density<R>(B, ctx->G, L, last);
+    launch_force<R>(B, ctx->G, L, last ? MODE_CLOSE : MODE_CLOSE_OPEN, last);
+}
+
+// Capture nsteps steps (the last one closing with energies when kind == 1)
+// into a graph.  Each step is [decide -> IF(rebuild) -> density -> force];
+// decide sets the IF node's condition on the device.
+template <class R>
+md_status build_graph(md_ctx *ctx, int kind, int nsteps, double dt, GraphEntry &out)
+{
+    const Bufs<R> &B = bufs<R>(ctx);
+    cudaStream_t cs = ctx->cap_stream;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int s = 0; s < nsteps; ++s) {
+        bool last = (kind == 1) && (s == nsteps - 1);
+        cudaStreamCaptureStatus status;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, &deps, nullptr, &ndeps));
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+        Launch L = ctx->L;
+        L.stream = cs;
+        L.cond = h;
+        L.use_cond = 1;
+        launch_decide<R>(B, L);
+        CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, &deps, nullptr, &ndeps));
+        alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+        memset(raw, 0, sizeof(raw));
+        cudaGraphNodeParams &p = *reinterpret_cast<cudaGraphNodeParams *>(raw);
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = h;
+        p.conditional.type = cudaGraphCondTypeIf;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &p));
+        CK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        CK(cudaStreamBeginCaptureToGraph(ctx->body_stream, body, nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal));
+        Launch Lb = L;
+        Lb.stream = ctx->body_stream;
+        launch_rebuild<R>(B, ctx->G, Lb);
+        CK(cudaStreamEndCapture(ctx->body_stream, &body));
+        launch_density<R>(B, ctx->G, L, last);
+        launch_force<R>(B, ctx->G, L, last ? MODE_CLOSE : MODE_CLOSE_OPEN, last);
+        if (last) launch_reduce<R>(B, L);
+    }
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamEndCapture(cs, &graph));
+    cudaGraphExec_t exec = nullptr;
+    CK(cudaGraphInstantiate(&exec, graph, 0));
+    out.kind = kind;
+    out.nsteps = nsteps;
+    out.dt = dt;
+    out.graph = graph;
+    out.exec = exec;
+    return MD_OK;
+}
+
+template <class R>
+md_status get_graph(md_ctx *ctx, int kind, int nsteps, double dt, cudaGraphExec_t &exec)
+{
+    for (auto &g : ctx->graphs)
+        if (g.kind == kind && g.nsteps == nsteps && g.dt == dt) {
+            exec = g.exec;
+            return MD_OK;
+        }
+    GraphEntry e{};
+    md_status rc = build_graph<R>(ctx, kind, nsteps, dt, e);
+    if (rc != MD_OK) return rc;
+    ctx->graphs.push_back(e);
+    exec = e.exec;
+    return MD_OK;
+}
+
+template <class R>
+md_status step_impl(md_ctx *ctx, int64_t nsteps, double dt)
+{
+    const Bufs<R> &B = bufs<R>(ctx);
+    ctx->L.dt = dt;
+    for (int t = 0; t < ctx->ntypes; ++t) ctx->L.half_kick[t] = 0.5 * dt * kAccel / ctx->mass[t];
+    Launch L = ctx->L;
+    L.use_cond = 0;
+    L.cond = 0;
+    ctx->fixed_launches += launch_open<R>(B, ctx->G, L);
+    if (!ctx->opt.use_graphs) {
+        for (int64_t s = 0; s < nsteps; ++s) {
+            enqueue_step<R>(ctx, L, s == nsteps - 1);
+            ctx->fixed_launches += 3 + 8;
+        }
+        ctx->fixed_launches += launch_reduce<R>(B, L);
+        CK(cudaGetLastError());
+        return MD_OK;
+    }
+    const int chunk = 10;
+    int64_t mid = nsteps - 1;
+    cudaGraphExec_t ex;
+    if (mid >= chunk) {
+        md_status rc = get_graph<R>(ctx, 0, chunk, dt, ex);
+        if (rc != MD_OK) return rc;
+        for (int64_t k = 0; k < mid / chunk; ++k) CK(cudaGraphLaunch(ex, ctx->stream));
+    }
+    if (mid % chunk) {
+        md_status rc = get_graph<R>(ctx, 0, (int)(mid % chunk), dt, ex);
+        if (rc != MD_OK) return rc;
+        CK(cudaGraphLaunch(ex, ctx->stream));
+    }
+    md_status rc = get_graph<R>(ctx, 1, 1, dt, ex);
+    if (rc != MD_OK) return rc;
+    CK(cudaGraphLaunch(ex, ctx->stream));
+    ctx->fixed_launches += 3 * nsteps + 1;
+    return MD_OK;
+}
+
+// Eager steps with events around each kernel group (see md_profile).
+template <class R>
+md_status profile_impl(md_ctx *ctx, int64_t nsteps, double dt, md_profile_t *out)
+{
+    const Bufs<R> &B = bufs<R>(ctx);
+    ctx->L.dt = dt;
+    for (int t = 0; t < ctx->ntypes; ++t) ctx->L.half_kick[t] = 0.5 * dt * kAccel / ctx->mass[t];
+    Launch L = ctx->L;
+    L.use_cond = 0;
+    L.cond = 0;
+    const int64_t ne = 4 * nsteps + 2;
+    std::vector<cudaEvent_t> ev(ne);
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    int64_t k = 0;
+    CK(cudaEventRecord(ev[k++], ctx->stream));
+    ctx->fixed_launches += launch_open<R>(B, ctx->G, L);
+    for (int64_t s = 0; s < nsteps; ++s) {
+        bool last = s == nsteps - 1;
+        ctx->fixed_launches += launch_decide<R>(B, L);
+        CK(cudaEventRecord(ev[k++], ctx->stream));
+        ctx->fixed_launches += launch_rebuild<R>(B, ctx->G, L);
+        CK(cudaEventRecord(ev[k++], ctx->stream));
+        ctx->fixed_launches += launch_density<R>(B, ctx->G, L, last);
+        CK(cudaEventRecord(ev[k++], ctx->stream));
+        ctx->fixed_launches += launch_force<R>(B, ctx->G, L, last ? MODE_CLOSE : MODE_CLOSE_OPEN, last);
+        CK(cudaEventRecord(ev[k++], ctx->stream));
+    }
+    ctx->fixed_launches += launch_reduce<R>(B, L);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    double dens = 0, force = 0, reb = 0, total = 0;
+    int64_t nreb = 0;
+    const double empty_rebuild_ms = 0.05;  // the 8 guarded kernels exit at once when no build is due
+    for (int64_t s = 0; s < nsteps; ++s) {
+        float a = 0, b = 0, c = 0;
+        CK(cudaEventElapsedTime(&a, ev[1 + 4 * s], ev[2 + 4 * s]));
+        CK(cudaEventElapsedTime(&b, ev[2 + 4 * s], ev[3 + 4 * s]));
+        CK(cudaEventElapsedTime(&c, ev[3 + 4 * s], ev[4 + 4 * s]));
+        if (a > empty_rebuild_ms) {
+            reb += a;
+            ++nreb;
+        }
+        dens += b;
+        force += c;
+    }
+    float tot = 0;
+    CK(cudaEventElapsedTime(&tot, ev[0], ev[4 * nsteps]));
+    total = tot;
+    for (auto &e : ev) cudaEventDestroy(e);
+    memset(out, 0, sizeof(*out));
+    out->density_ms = dens / (double)nsteps;
+    out->force_ms = force / (double)nsteps;
+    out->rebuild_ms = nreb ? reb / (double)nreb : 0.0;
+    out->step_ms = total / (double)nsteps;
+    out->density_launches = nsteps;
+    out->force_launches = nsteps;
+    out->rebuilds = nreb;
+    return MD_OK;
+}
+
+template <class R>
+md_status store_state(md_ctx *ctx, double *pos, double *vel, double *force)
+{
+    const size_t n = (size_t)ctx->n;
+    if (n == 0) return MD_OK;
+    Launch L = ctx->L;
+    double *dp = pos ? ctx->stage : nullptr;
+    double *dv = vel ? ctx->stage + 3 * n : nullptr;
+    double *df = force ? ctx->stage + 6 * n : nullptr;
+    ctx->fixed_launches += launch_store_state<R>(bufs<R>(ctx), L, dp, dv, df);
+    CK(cudaGetLastError());
+    if (pos) CK(cudaMemcpyAsync(pos, dp, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (vel) CK(cudaMemcpyAsync(vel, dv, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (force) CK(cudaMemcpyAsync(force, df, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MD_OK;
+}
+
+template <class R>
+md_status create_impl(md_ctx *ctx, const double *pos, const double *vel, const int32_t *types,
+                      const md_potential *pot)
+{
+    // spline tables: f[t], F[t], phi[q] appended into one coefficient array
+    std::vector<double> rows;
+    Tables<R> tab;
+    memset(&tab, 0, sizeof(tab));
+    tab.ntypes = pot->ntypes;
+    auto add = [&](const md_spline &s, SplineDesc<R> &d) -> bool {
+        int off = (int)(rows.size() / 4);
+        if (!hermite_coefficients(s, rows)) return false;
+        d = make_desc<R>(s, off, &rows[rows.size() - 4], &rows[4 * (size_t)off]);
+        return true;
+    };
+    int npair = pot->ntypes * (pot->ntypes + 1) / 2;
+    for (int t = 0; t < pot->ntypes; ++t) {
+        if (!add(pot->F[t], tab.F[t]) || !add(pot->f[t], tab.f[t]))
+            return ctx->fail(MD_ERR_ARG, "spline system is singular");
+    }
+    for (int q = 0; q < npair; ++q)
+        if (!add(pot->phi[q], tab.phi[q])) return ctx->fail(MD_ERR_ARG, "spline system is singular");
+
+    CK(cudaMallocHost((void **)&ctx->st_host, sizeof(DevState)));
+    if (!alloc_n(ctx, ctx->st, 1) || !alloc_n(ctx, ctx->stage, 9 * (size_t)std::max<int64_t>(ctx->n, 1)) ||
+        !alloc_n(ctx, ctx->types_orig, (size_t)std::max<int64_t>(ctx->n, 1)))
+        return ctx->fail(MD_ERR_OOM, "device allocation failed");
+    if (!alloc_buffers<R>(ctx, rows, tab)) return ctx->fail(MD_ERR_OOM, "device allocation failed");
+    DevState h{};
+    CK(cudaMemcpy(ctx->st, &h, sizeof(DevState), cudaMemcpyHostToDevice));
+    if (ctx->n == 0) return MD_OK;
+    CK(cudaMemcpy(ctx->types_orig, types, sizeof(int32_t) * (size_t)ctx->n, cudaMemcpyHostToDevice));
+    return load_and_measure<R>(ctx, pos, vel, 0);
+}
+
+}  // namespace
+
+// ==========================================================================
+// C ABI
+
+extern "C" {
+
+void md_options_default(md_options *opt)
+{
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->precision = MD_PRECISION_MIXED;
+    opt->rebuild_every = 10;
+    opt->list_capacity = 0;
+    opt->use_graphs = 1;
+    opt->block_size = 256;
+}
+
+md_status md_create(const double box[3], int64_t n, const double *pos, const double *vel,
+                    const int32_t *types, const md_potential *pot, const md_options *opt, md_ctx **out)
+{
+    g_create_error.clear();
+    auto bad = [](md_status s, const char *m) {
+        g_create_error = m;
+        return s;
+    };
+    if (!out) return bad(MD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!box || !pot || n < 0 || (n > 0 && (!pos || !types))) return bad(MD_ERR_ARG, "null argument or n < 0");
+    if (n >= (int64_t)kIndexMask) return bad(MD_ERR_CAPACITY, "n must be below 2^27");
+    if (pot->ntypes < 1 || pot->ntypes > kMaxTypes || !pot->mass || !pot->F || !pot->f || !pot->phi)
+        return bad(MD_ERR_ARG, "potential: ntypes must be 1..8 and all tables given");
+    if (!(pot->r_cut > 0.0) || !(pot->skin >= 0.0) || !std::isfinite(pot->r_cut) || !std::isfinite(pot->skin))
+        return bad(MD_ERR_ARG, "r_cut must be > 0 and skin >= 0");
+    const double r_list = pot->r_cut + pot->skin;
+    for (int t = 0; t < pot->ntypes; ++t) {
+        if (!(pot->mass[t] > 0.0) || !std::isfinite(pot->mass[t])) return bad(MD_ERR_ARG, "masses must be > 0");
+        if (!spline_ok(pot->F[t]) || !spline_ok(pot->f[t])) return bad(MD_ERR_ARG, "bad F or f spline");
+        const md_spline &f = pot->f[t];
+        if (f.x0 > 0.0 || f.x0 + (f.n - 1) * f.dx < pot->r_cut)
+            return bad(MD_ERR_ARG, "f tables must cover [0, r_cut]");
+    }
+    for (int q = 0; q < pot->ntypes * (pot->ntypes + 1) / 2; ++q) {
+        const md_spline &s = pot->phi[q];
+        if (!spline_ok(s)) return bad(MD_ERR_ARG, "bad phi spline");
+        if (s.x0 > 0.0 || s.x0 + (s.n - 1) * s.dx < pot->r_cut)
+            return bad(MD_ERR_ARG, "phi tables must cover [0, r_cut]");
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (!(box[a] > 0.0) || !std::isfinite(box[a])) return bad(MD_ERR_ARG, "box edges must be > 0");
+        if (std::floor(box[a] / r_list) < 3.0) return bad(MD_ERR_BOX, "box edge shorter than 3 (r_cut + skin)");
+    }
+    for (int64_t i = 0; i < 3 * n; ++i) {
+        if (!std::isfinite(pos[i]) || (vel && !std::isfinite(vel[i])))
+            return bad(MD_ERR_NONFINITE, "non-finite position or velocity");
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (types[i] < 0 || types[i] >= pot->ntypes) return bad(MD_ERR_ARG, "atom type out of range");
+    md_options o;
+    md_options_default(&o);
+    if (opt) o = *opt;
+    if (o.precision != MD_PRECISION_FP64 && o.precision != MD_PRECISION_MIXED)
+        return bad(MD_ERR_ARG, "precision must be 0 (FP64) or 1 (mixed)");
+    if (o.rebuild_every < 1) o.rebuild_every = 10;
+    if (o.block_size <= 0) o.block_size = 256;
+    if (o.block_size > 256 || (o.block_size & 31)) return bad(MD_ERR_ARG, "block_size must be a multiple of 32, <= 256");
+    if ((o.alloc == nullptr) != (o.free == nullptr)) return bad(MD_ERR_ARG, "alloc and free go together");
+
+    md_ctx *ctx = new (std::nothrow) md_ctx();
+    if (!ctx) return bad(MD_ERR_OOM, "host allocation failed");
+    ctx->opt = o;
+    ctx->precision = o.precision;
+    ctx->n = n;
+    ctx->ntypes = pot->ntypes;
+    for (int t = 0; t < pot->ntypes; ++t) ctx->mass[t] = pot->mass[t];
+    memcpy(ctx->box, box, sizeof(ctx->box));
+    if (o.cuda_stream) {
+        ctx->stream = (cudaStream_t)o.cuda_stream;
+    } else if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) == cudaSuccess) {
+        ctx->own_stream = true;
+    } else {
+        delete ctx;
+        return bad(MD_ERR_CUDA, "cannot create a CUDA stream");
+    }
+    if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        md_destroy(ctx);
+        return bad(MD_ERR_CUDA, "cannot create a CUDA stream");
+    }
+
+    // geometry: cells of edge >= r_list, at least 3 per axis
+    Geom &G = ctx->G;
+    double hmax = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        G.box[a] = box[a];
+        G.half_box[a] = 0.5 * box[a];
+        G.ncell[a] = (int)std::floor(box[a] / r_list);
+        G.inv_cell[a] = (double)G.ncell[a] / box[a];
+        G.h[a] = box[a] / (double)G.ncell[a];
+        hmax = std::max(hmax, G.h[a]);
+    }
+    G.ncells = G.ncell[0] * G.ncell[1] * G.ncell[2];
+    G.rl2 = r_list * r_list;
+    G.rc2 = pot->r_cut * pot->r_cut;
+    // rounding bound of the screened r^2 (cell-relative coordinates, |u| <= h)
+    const double eps = (o.precision == MD_PRECISION_MIXED) ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+    const double margin = 8.0 * (20.0 * hmax * r_list + 4.0 * r_list * r_list) * eps;
+    G.screen_lo = G.rl2 - margin;
+    G.screen_hi = G.rl2 + margin;
+
+    Launch &L = ctx->L;
+    L.n = (int)n;
+    L.ld = (int)((n + 31) / 32 * 32);
+    L.block = o.block_size;
+    L.nblocks = (int)((n + L.block - 1) / L.block);
+    L.ntypes = pot->ntypes;
+    L.rebuild_every = o.rebuild_every;
+    L.disp2_thr = 0.25 * pot->skin * pot->skin;
+    L.stream = ctx->stream;
+    for (int t = 0; t < pot->ntypes; ++t) L.ke_factor[t] = 0.5 * pot->mass[t] / kAccel;
+    if (o.list_capacity > 0) {
+        L.cap = o.list_capacity;
+    } else {
+        double vol = box[0] * box[1] * box[2];
+        double expect = (double)n / vol * 4.0 / 3.0 * M_PI * r_list * r_list * r_list;
+        L.cap = std::max(16, ((int)std::ceil(1.25 * expect) + 8 + 3) & ~3);
+    }
+
+    md_status rc = (o.precision == MD_PRECISION_MIXED) ? create_impl<float>(ctx, pos, vel, types, pot)
+                                                       : create_impl<double>(ctx, pos, vel, types, pot);
+    if (rc != MD_OK) {
+        g_create_error = ctx->err;
+        md_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return MD_OK;
+}
+
+md_status md_step(md_ctx *ctx, int64_t nsteps, double dt)
+{
+    if (!ctx) return MD_ERR_ARG;
+    if (nsteps < 0 || !std::isfinite(dt)) return ctx->fail(MD_ERR_ARG, "nsteps must be >= 0 and dt finite");
+    if (nsteps == 0) return MD_OK;
+    if (ctx->n == 0) {
+        ctx->host_steps += nsteps;
+        return MD_OK;
+    }
+    return ctx->precision == MD_PRECISION_MIXED ? step_impl<float>(ctx, nsteps, dt)
+                                                : step_impl<double>(ctx, nsteps, dt);
+}
+
+md_status md_sync(md_ctx *ctx)
+{
+    if (!ctx) return MD_ERR_ARG;
+    if (ctx->n == 0) return MD_OK;
+    return check_device_errors(ctx);
+}
+
+md_status md_energy(md_ctx *ctx, double *pe, double *ke)
+{
+    if (!ctx) return MD_ERR_ARG;
+    if (ctx->n == 0) {
+        if (pe) *pe = 0.0;
+        if (ke) *ke = 0.0;
+        return MD_OK;
+    }
+    md_status rc = check_device_errors(ctx);
+    if (rc != MD_OK) return rc;
+    if (pe) *pe = ctx->st_host->e_embed + ctx->st_host->e_pair;
+    if (ke) *ke = ctx->st_host->ke;
+    return MD_OK;
+}
+
+md_status md_virial(md_ctx *ctx, double w[6])
+{
+    if (!ctx || !w) return ctx ? ctx->fail(MD_ERR_ARG, "w is NULL") : MD_ERR_ARG;
+    if (ctx->n == 0) {
+        for (int k = 0; k < 6; ++k) w[k] = 0.0;
+        return MD_OK;
+    }
+    md_status rc = check_device_errors(ctx);
+    if (rc != MD_OK) return rc;
+    for (int k = 0; k < 6; ++k) w[k] = ctx->st_host->virial[k];
+    return MD_OK;
+}
+
+md_status md_forces(md_ctx *ctx, double *f)
+{
+    if (!ctx || !f) return ctx ? ctx->fail(MD_ERR_ARG, "f is NULL") : MD_ERR_ARG;
+    md_status rc = md_sync(ctx);
+    if (rc != MD_OK) return rc;
+    return ctx->precision == MD_PRECISION_MIXED ? store_state<float>(ctx, nullptr, nullptr, f)
+                                                : store_state<double>(ctx, nullptr, nullptr, f);
+}
+
+md_status md_get_state(md_ctx *ctx, double *pos, double *vel, int64_t *step)
+{
+    if (!ctx) return MD_ERR_ARG;
+    md_status rc = md_sync(ctx);
+    if (rc != MD_OK) return rc;
+    if (step) *step = ctx->n == 0 ? ctx->host_steps : (int64_t)ctx->st_host->step;
+    if (!pos && !vel) return MD_OK;
+    return ctx->precision == MD_PRECISION_MIXED ? store_state<float>(ctx, pos, vel, nullptr)
+                                                : store_state<double>(ctx, pos, vel, nullptr);
+}
+
+md_status md_set_state(md_ctx *ctx, const double *pos, const double *vel, int64_t step)
+{
+    if (!ctx) return MD_ERR_ARG;
+    if (ctx->n == 0) {
+        ctx->host_steps = step;
+        return MD_OK;
+    }
+    if (!pos) return ctx->fail(MD_ERR_ARG, "pos is NULL");
+    for (int64_t i = 0; i < 3 * ctx->n; ++i)
+        if (!std::isfinite(pos[i]) || (vel && !std::isfinite(vel[i])))
+            return ctx->fail(MD_ERR_NONFINITE, "non-finite position or velocity");
+    return ctx->precision == MD_PRECISION_MIXED ? load_and_measure<float>(ctx, pos, vel, step)
+                                                : load_and_measure<double>(ctx, pos, vel, step);
+}
+
+md_status md_neighbors(md_ctx *ctx, int64_t *offsets, int32_t *js, int64_t cap)
+{
+    if (!ctx || !offsets) return ctx ? ctx->fail(MD_ERR_ARG, "offsets is NULL") : MD_ERR_ARG;
+    const int64_t n = ctx->n;
+    if (n == 0) {
+        offsets[0] = 0;
+        return MD_OK;
+    }
+    md_status rc = md_sync(ctx);
+    if (rc != MD_OK) return rc;
+    const int set = ctx->st_host->set;
+    std::vector<int> nnb(n), id(n);
+    std::vector<uint32_t> list((size_t)ctx->L.cap * ctx->L.ld);
+    const int *idp = ctx->precision == MD_PRECISION_MIXED ? ctx->Bf.id[set] : ctx->Bd.id[set];
+    const int *nnbp = ctx->precision == MD_PRECISION_MIXED ? ctx->Bf.nnb : ctx->Bd.nnb;
+    const uint32_t *lp = ctx->precision == MD_PRECISION_MIXED ? ctx->Bf.list : ctx->Bd.list;
+    CK(cudaMemcpy(nnb.data(), nnbp, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(id.data(), idp, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(list.data(), lp, sizeof(uint32_t) * list.size(), cudaMemcpyDeviceToHost));
+    std::vector<int64_t> cnt(n + 1, 0);
+    for (int64_t p = 0; p < n; ++p) cnt[id[p]] = nnb[p];
+    offsets[0] = 0;
+    for (int64_t i = 0; i < n; ++i) offsets[i + 1] = offsets[i] + cnt[i];
+    if (js && offsets[n] <= cap) {
+        for (int64_t p = 0; p < n; ++p) {
+            int64_t o = offsets[id[p]];
+            for (int k = 0; k < nnb[p]; ++k) js[o + k] = id[list[(size_t)k * ctx->L.ld + p] & kIndexMask];
+        }
+    }
+    return MD_OK;
+}
+
+md_status md_cells(md_ctx *ctx, int32_t ncell[3], int32_t *cell_start, int32_t *cell_atoms)
+{
+    if (!ctx) return MD_ERR_ARG;
+    if (ncell)
+        for (int a = 0; a < 3; ++a) ncell[a] = ctx->G.ncell[a];
+    if (!cell_start && !cell_atoms) return MD_OK;
+    if (ctx->n == 0) {
+        if (cell_start) memset(cell_start, 0, sizeof(int32_t) * ((size_t)ctx->G.ncells + 1));
+        return MD_OK;
+    }
+    md_status rc = md_sync(ctx);
+    if (rc != MD_OK) return rc;
+    const int set = ctx->st_host->set;
+    const int *csp = ctx->precision == MD_PRECISION_MIXED ? ctx->Bf.cell_start : ctx->Bd.cell_start;
+    const int *idp = ctx->precision == MD_PRECISION_MIXED ? ctx->Bf.id[set] : ctx->Bd.id[set];
+    if (cell_start) CK(cudaMemcpy(cell_start, csp, sizeof(int) * ((size_t)ctx->G.ncells + 1), cudaMemcpyDeviceToHost));
+    if (cell_atoms) CK(cudaMemcpy(cell_atoms, idp, sizeof(int) * (size_t)ctx->n, cudaMemcpyDeviceToHost));
+    return MD_OK;
+}
+
+md_status md_stats(md_ctx *ctx, md_stats_t *out)
+{
+    if (!ctx || !out) return ctx ? ctx->fail(MD_ERR_ARG, "out is NULL") : MD_ERR_ARG;
+    memset(out, 0, sizeof(*out));
+    out->list_capacity = ctx->L.cap;
+    if (ctx->n == 0) {
+        out->steps = ctx->host_steps;
+        return MD_OK;
+    }
+    md_status rc = read_state(ctx);
+    if (rc != MD_OK) return rc;
+    const DevState &h = *ctx->st_host;
+    out->steps = h.step;
+    out->rebuilds = h.rebuilds - ctx->rebuilds_at_create;
+    out->max_neighbors = h.max_nnb;
+    out->table_out_of_range = (int64_t)h.table_oor;
+    out->kernel_launches = ctx->fixed_launches + 8 * h.graph_rebuilds;
+    return MD_OK;
+}
+
+md_status md_profile(md_ctx *ctx, int64_t nsteps, double dt, md_profile_t *out)
+{
+    if (!ctx || !out) return ctx ? ctx->fail(MD_ERR_ARG, "out is NULL") : MD_ERR_ARG;
+    if (nsteps < 1 || !std::isfinite(dt)) return ctx->fail(MD_ERR_ARG, "nsteps must be >= 1 and dt finite");
+    memset(out, 0, sizeof(*out));
+    if (ctx->n == 0) return MD_OK;
+    md_status rc = ctx->precision == MD_PRECISION_MIXED ? profile_impl<float>(ctx, nsteps, dt, out)
+                                                        : profile_impl<double>(ctx, nsteps, dt, out);
+    if (rc != MD_OK) return rc;
+    return check_device_errors(ctx);
+}
+
+const char *md_last_error(const md_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+void md_destroy(md_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    drop_graphs(ctx);
+    dfree_all(ctx);
+    if (ctx->st_host) cudaFreeHost(ctx->st_host);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// md_internal.cuh -- device data layout shared by the kernels and the host
+// runtime of the EAM library (not part of the public ABI).
+//
+// Layout in HBM (all per-atom arrays in the current spatially sorted order,
+// i.e. grouped by cell, ascending original id inside a cell):
+//   xr[set][3]   FP64 SoA, wrapped absolute positions at the last list build
+//   d[3]         FP64 SoA, displacement since the last build (x = xr + d)
+//   v[set][3]    FP64 SoA, velocities
+//   id[set], type[set]   int32: original index and atom type
+//   uref[3]      R SoA, xr minus the centre of the atom's cell (|uref| <= h/2)
+//   shadow[2]    R4 (u_x, u_y, u_z, 0), u = uref + d: the coordinates the pair
+//                kernels read; double-buffered across steps
+//   Fp           R, embedding derivative F'(rho_i) of the current step
+//   fcache[3]    R SoA, forces of the last closed step
+//   list         uint32 [capacity][ld] (column k of atom i at k*ld + i):
+//                neighbour index in bits 0..26, stencil code in bits 27..31
+//   nnb          int32 neighbours per atom
+// "set" flips at every list build (the permutation writes the other set),
+// "sp" flips at every drift.  Both live in DevState, on the device, so that a
+// captured CUDA graph replays correctly whatever the rebuild history.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace eammd {
+
+constexpr int kMaxTypes = 8;
+constexpr int kMaxPairs = kMaxTypes * (kMaxTypes + 1) / 2;
+constexpr int kCodeShift = 27;
+constexpr uint32_t kIndexMask = (1u << kCodeShift) - 1u;
+constexpr int kScanBlock = 1024;
+constexpr int kEnergySlots = 10;  // embed, pair, ke, virial xx yy zz xy xz yz, spare
+constexpr double kAccel = 9.648533215665e-3;  // (eV/Angstrom/amu) -> Angstrom/fs^2
+
+enum : uint32_t { ERR_LIST_OVERFLOW = 1u, ERR_NONFINITE = 2u, ERR_TIMEOUT = 4u };
+
+struct DevState {
+    long long step;
+    long long rebuilds;
+    unsigned long long table_oor;
+    int since_build;
+    int sp;
+    int set;
+    int need_rebuild;
+    unsigned int maxdisp2;  // bit pattern of a non-negative float (orders as unsigned)
+    unsigned int error;
+    int max_nnb;
+    int pad0;
+    long long graph_rebuilds;  // builds run inside a graph's conditional node
+    double e_embed, e_pair, ke;
+    double virial[6];
+};
+
+template <class R> struct V4;
+template <> struct V4<float> { using T = float4; };
+template <> struct V4<double> { using T = double4_32a; };
+
+// One cubic spline on uniform knots: coefficients (a, b, c, d) of interval k
+// at coef[offset + k], S(t) = a + b t + c t^2 + d t^3 with t = x - x_k.
+template <class R>
+struct SplineDesc {
+    int offset, nint;
+    R x0, inv_h;
+    R h_hi, h_lo;        // h = h_hi + h_lo (the knot spacing to FP64 accuracy in R pairs)
+    R x_end;             // last knot
+    R y_lo, s_lo;        // value and slope at x0 (continued linearly below)
+    R y_end, s_end;      // value and slope at x_end (continued linearly above)
+};
+
+template <class R>
+struct Tables {
+    int ntypes;
+    SplineDesc<R> F[kMaxTypes], f[kMaxTypes], phi[kMaxPairs];
+};
+
+struct Geom {
+    double box[3];
+    double half_box[3];
+    double inv_cell[3];  // n_d / L_d
+    double h[3];         // L_d / n_d
+    int ncell[3];
+    int ncells;
+    double rl2;          // r_list^2
+    double screen_lo;    // candidates with r2 below this are in the list for sure
+    double screen_hi;    // ... above this are out for sure; in between: exact FP64 test
+    double rc2;          // r_cut^2
+};
+
+template <class R>
+struct Bufs {
+    using R4 = typename V4<R>::T;
+    double *xr[2][3];
+    double *d[3];
+    double *v[2][3];
+    int *id[2];
+    int *type[2];
+    R *uref[3];
+    R4 *shadow[2];
+    R *Fp;
+    R *fcache[3];
+    int *cell;
+    double *center[3];   // cell centres per axis, (c + 1/2) h_d
+    // rebuild scratch
+    double *xw[3];
+    int *cell_old;
+    int *slot;
+    int *count;
+    int *cell_start;
+    int *cell_atoms;
+    int *block_sums;
+    // list
+    uint32_t *list;
+    int *nnb;
+    // energy partials [kEnergySlots][nblocks]
+    double *partials;
+    // state and tables
+    DevState *st;
+    const R4 *coef;
+    const Tables<R> *tables;
+};
+
+struct Launch {
+    int n;          // atoms
+    int ld;         // list leading dimension (multiple of 32)
+    int cap;        // list slots per atom
+    int block;      // threads per block of per-atom kernels
+    int nblocks;    // ceil(n / block)
+    int ntypes;
+    int rebuild_every;
+    double disp2_thr;                 // (skin/2)^2
+    double dt;
+    double half_kick[kMaxTypes];      // 0.5 dt kAccel / m_t
+    double ke_factor[kMaxTypes];      // 0.5 m_t / kAccel
+    cudaStream_t stream;
+    cudaGraphConditionalHandle cond;  // 0 outside graph capture
+    int use_cond;
+};
+
+enum StepMode { MODE_MEASURE = 0, MODE_CLOSE = 1, MODE_CLOSE_OPEN = 2 };
+
+// Host-side launchers (kernels.cu).  All are asynchronous on L.stream and
+// return the number of kernels queued.
+template <class R> int launch_rebuild(const Bufs<R> &B, const Geom &G, const Launch &L);
+template <class R> int launch_decide(const Bufs<R> &B, const Launch &L);
+template <class R> int launch_open(const Bufs<R> &B, const Geom &G, const Launch &L);
+template <class R> int launch_density(const Bufs<R> &B, const Geom &G, const Launch &L, bool energy);
+template <class R> int launch_force(const Bufs<R> &B, const Geom &G, const Launch &L, int mode, bool energy);
+template <class R> int launch_reduce(const Bufs<R> &B, const Launch &L);
+template <class R>
+int launch_load_state(const Bufs<R> &B, const Launch &L, const double *pos, const double *vel, const int *types);
+template <class R>
+int launch_store_state(const Bufs<R> &B, const Launch &L, double *pos, double *vel, double *force);
+
+}  // namespace eammd

@@ -1,0 +1,67 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports
+every entry point that include/*.h declares (no compute calls here)."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2405_07898_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(md_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_declares_the_binding_exports():
+    names = declared_functions()
+    assert names == set(binding.EXPORTS), names ^ set(binding.EXPORTS)
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    assert os.path.exists(path)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = declared_functions() - exported
+    assert not missing, missing
+    lib = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert getattr(lib, name) is not None
+
+
+def test_options_default_without_gpu():
+    lib = binding.load()
+    opt = binding.Options()
+    lib.md_options_default(ctypes.byref(opt))
+    assert opt.precision == 1 and opt.rebuild_every == 10 and opt.use_graphs == 1
+    assert opt.block_size == 256 and opt.list_capacity == 0
+
+
+def test_create_rejects_bad_arguments_before_touching_the_gpu():
+    """Argument checks run on the host before any CUDA call."""
+    from paper_2405_07898_gb300 import inputs as I
+    s = I.bcc_2000_fp64()
+    small = I.System(box=s.box / 3.0, pos=s.pos / 3.0, vel=s.vel, types=s.types, pot=s.pot)
+    with pytest.raises(binding.MDError) as e:
+        binding.MD(small, use_torch=False)
+    assert e.value.status == -2  # MD_ERR_BOX
+    bad = I.System(box=s.box, pos=s.pos.copy(), vel=s.vel, types=s.types, pot=s.pot)
+    bad.pos[5, 1] = float("nan")
+    with pytest.raises(binding.MDError) as e:
+        binding.MD(bad, use_torch=False)
+    assert e.value.status == -5  # MD_ERR_NONFINITE
+    wrong_type = I.System(box=s.box, pos=s.pos, vel=s.vel, types=s.types + 3, pot=s.pot)
+    with pytest.raises(binding.MDError) as e:
+        binding.MD(wrong_type, use_torch=False)
+    assert e.value.status == -1  # MD_ERR_ARG
