@@ -193,6 +193,32 @@ typedef struct {
 
 md_status md_profile(md_ctx *ctx, int64_t nsteps, double dt, md_profile_t *out);
 
+/* Cell binning that allocates no device memory.  The paper has no
+ * counterpart: this is a service for callers that cannot call cudaMalloc --
+ * programs whose device memory is handed out by a fixed pool or budget that
+ * may not grow (a framework's caching allocator, an embedded or real-time
+ * loop that forbids allocation after start-up because cudaMalloc can
+ * synchronise the device).
+ * It computes what md_cells reports after md_create for the same positions:
+ * wraps d_pos (n*3 doubles, xyz interleaved, device memory) into the box,
+ * uses ncell_d = floor(box_d / r_list) cells per axis (each >= 3), and writes
+ * d_cell_start[ncells+1] and d_cell_atoms[n] (atom indices, ascending inside
+ * each cell; both device memory, caller-owned), queued on cuda_stream (NULL =
+ * the legacy default stream); it does not synchronise.
+ * Scratch lives in one static device array of about 2.4 MB that every GPU
+ * loading this library holds until the process exits.  Limits: n <= 262,144
+ * atoms and ncells <= 65,536; larger inputs return MD_ERR_CAPACITY, and no
+ * work is queued.  Other errors: MD_ERR_ARG, MD_ERR_BOX (an axis with fewer
+ * than 3 cells), MD_ERR_CUDA; this entry point has no context, so
+ * md_last_error() does not describe its failures.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the one array: calls that
+ * overlap on the GPU (different streams, or different host threads on the
+ * same device) race and must be ordered by the caller. */
+md_status md_bin_cells_noalloc(const double box[3], double r_list, int64_t n, const double *d_pos,
+                               int32_t *d_cell_start, int32_t *d_cell_atoms, void *cuda_stream);
+
 /* Message for the last failed call on ctx (or of md_create when ctx is NULL). */
 const char *md_last_error(const md_ctx *ctx);
 

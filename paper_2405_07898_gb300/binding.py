@@ -28,7 +28,7 @@ PRECISION = {"fp64": 0, "mixed": 1}
 # every entry point declared in include/eammd.h
 EXPORTS = ("md_options_default", "md_create", "md_step", "md_sync", "md_energy", "md_forces",
            "md_virial", "md_get_state", "md_set_state", "md_neighbors", "md_cells", "md_stats",
-           "md_profile", "md_last_error", "md_destroy")
+           "md_profile", "md_last_error", "md_destroy", "md_bin_cells_noalloc")
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -119,6 +119,9 @@ def load(build_if_missing: bool = True):
     L.md_last_error.restype = C.c_char_p
     L.md_destroy.argtypes = [C.c_void_p]
     L.md_destroy.restype = None
+    L.md_bin_cells_noalloc.argtypes = [_dp, C.c_double, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p]
+    L.md_bin_cells_noalloc.restype = C.c_int
     _lib = L
     return L
 
@@ -153,6 +156,17 @@ def _torch_allocator(stream):
         torch.cuda.caching_allocator_delete(int(ptr))
 
     return ALLOC_FN(alloc), FREE_FN(free)
+
+
+def bin_cells_noalloc(box, r_list: float, n: int, d_pos: int, d_cell_start: int, d_cell_atoms: int,
+                      stream: int = 0) -> int:
+    """md_bin_cells_noalloc: cell bins of n device positions into caller-owned
+    device arrays, without any device allocation.  Pointers are integers
+    (e.g. torch `data_ptr()`); returns the md_status code."""
+    L = load()
+    box = _f64(box)
+    return L.md_bin_cells_noalloc(_d(box), float(r_list), int(n), C.c_void_p(d_pos),
+                                  C.c_void_p(d_cell_start), C.c_void_p(d_cell_atoms), C.c_void_p(stream))
 
 
 class MD:
