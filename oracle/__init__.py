@@ -81,6 +81,11 @@ def lib():
         L.orc_sys_energy.argtypes = [C.c_void_p, _dp, _dp]
         L.orc_sys_virial.argtypes = [C.c_void_p, _dp]
         L.orc_sys_get.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, _dp, _lp]
+        L.orc_spline_basis.argtypes = [C.c_int32, C.c_double, C.c_int32, C.c_int32, _dp]
+        L.orc_spline_basis.restype = C.c_int
+        L.orc_force_match.argtypes = [C.c_void_p, C.c_int64, _dp, _dp, C.c_double, _dp, C.c_double, _dp,
+                                      _dp, _dp, _dp, _dp, _dp]
+        L.orc_force_match.restype = C.c_int
         _lib = L
     return _lib
 
@@ -284,3 +289,53 @@ class System:
         if h and _lib is not None:
             _lib.orc_sys_destroy(h)
             self.handle = None
+
+
+# --------------------------------------------------------------------------
+# differentiation (force matching)
+
+
+def spline_basis(knots) -> np.ndarray:
+    """M with coefficients = M @ y (+ the end-slope part): shape (4(n-1), n)."""
+    M = np.zeros((4 * (knots.n - 1), knots.n))
+    rc = lib().orc_spline_basis(knots.n, knots.dx, knots.bc_lo, knots.bc_hi, _d(M))
+    if rc:
+        raise ValueError("spline basis failed")
+    return M
+
+
+def force_match(pot: Potential, pos, box, e_ref: float, f_ref, w: float):
+    """Loss (E - E_ref)^2/N + w sum |F - F_ref|^2 of one single-type
+    configuration and dL/d(coefficients) of phi, f, F (each (n-1, 4)); also
+    returns E and F."""
+    pos = _f64(pos)
+    n = pos.shape[0]
+    src = pot.src
+    g_phi = np.zeros((src.phi[0].n - 1, 4))
+    g_f = np.zeros((src.f[0].n - 1, 4))
+    g_F = np.zeros((src.F[0].n - 1, 4))
+    loss = C.c_double()
+    e = C.c_double()
+    force = np.zeros((n, 3))
+    rc = lib().orc_force_match(pot.handle, n, _d(_f64(box)), _d(pos), float(e_ref), _d(_f64(f_ref)),
+                               float(w), C.byref(loss), _d(g_phi), _d(g_f), _d(g_F), C.byref(e),
+                               _d(force))
+    if rc:
+        raise RuntimeError(f"force_match failed ({rc})")
+    return loss.value, (g_phi, g_f, g_F), e.value, force
+
+
+def force_match_knot_grad(pot: Potential, configs, w: float):
+    """Total loss over configs [(pos, box, e_ref, f_ref)] and its gradient
+    with respect to the knot values of phi, f and F (concatenated in that
+    order): the coefficient gradient mapped through M^T."""
+    src = pot.src
+    Ms = [spline_basis(src.phi[0]), spline_basis(src.f[0]), spline_basis(src.F[0])]
+    total = 0.0
+    gk = [np.zeros(src.phi[0].n), np.zeros(src.f[0].n), np.zeros(src.F[0].n)]
+    for pos, box, e_ref, f_ref in configs:
+        loss, gc, _, _ = force_match(pot, pos, box, e_ref, f_ref, w)
+        total += loss
+        for q in range(3):
+            gk[q] += Ms[q].T @ gc[q].ravel()
+    return total, np.concatenate(gk)

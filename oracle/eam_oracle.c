@@ -612,3 +612,161 @@ void orc_sys_get(const orc_sys *s, double *pos, double *vel, double *force, doub
     if (Fp) memcpy(Fp, s->Fp, sizeof(double) * (size_t)s->n);
     if (counters) { counters[0] = s->step; counters[1] = s->rebuilds; }
 }
+
+/* ------------------------------------------------------------------------ */
+/* differentiation: force-matching loss and its gradient                    */
+/*
+ * Loss of one configuration (single atom type):
+ *   L = (E - E_ref)^2 / N + w sum_i |F_i - F_ref,i|^2,
+ * with E of Eq. 3 and F of Eq. 4.  Every spline is linear in its per-interval
+ * coefficients (a, b, c, d), so dL/d(coefficients) is accumulated here and the
+ * knot gradient follows as M^T times it (orc_spline_basis gives M).
+ *
+ * With A = 2 (E - E_ref) / N, g_i = F_i - F_ref,i, and for the position
+ * perturbation dx = g:  dr_ij = (x_j - x_i)/r . (g_j - g_i),
+ * drho_i = sum_j f'(r_ij) dr_ij.  Since F = -dE/dx,
+ *   dL = A dE/dtheta - 2 w D_g[dE/dtheta]  (D_g: derivative along dx = g),
+ * where
+ *   dE/dtheta(phi) = 1/2 sum_{i != j} B(r_ij)       D_g = 1/2 sum B'(r_ij) dr_ij
+ *   dE/dtheta(F)   = sum_i B(rho_i)                  D_g = sum_i B'(rho_i) drho_i
+ *   dE/dtheta(f)   = sum_i F'(rho_i) sum_j B(r_ij)
+ *            D_g = sum_i [F''(rho_i) drho_i sum_j B(r_ij) + F'(rho_i) sum_j B'(r_ij) dr_ij]
+ * and for a coefficient row (a, b, c, d) of the interval holding x, B = (1, t,
+ * t^2, t^3) and B' = (0, 1, 2t, 3t^2), t = x - x_k.
+ */
+
+/* Interval and local coordinate of x on a spline (beyond the ends: the end
+ * interval; then the coefficient derivative rows below are those of the
+ * linear continuation, which depends on the end interval only). */
+static int64_t seg_of(const orc_spline *s, double x, double *t)
+{
+    int64_t k;
+    if (x < s->x0) k = 0;
+    else {
+        k = (int64_t)floor((x - s->x0) / s->h);
+        if (k > s->n - 2) k = s->n - 2;
+    }
+    *t = x - (s->x0 + (double)k * s->h);
+    return k;
+}
+
+/* d(value)/d(a,b,c,d) and d(derivative)/d(a,b,c,d) at x, following
+ * orc_spline_eval: inside the table the cubic; outside, the tangent line at
+ * the end knot (value y_end + s_end (x - x_end), slope s_end). */
+static void coef_rows(const orc_spline *s, double x, int64_t *k, double bv[4], double bd[4])
+{
+    double t;
+    double x_end = s->x0 + (double)(s->n - 1) * s->h;
+    *k = seg_of(s, x, &t);
+    if (x < s->x0) {
+        /* y_0 + b_0 (x - x0): a and b of interval 0 */
+        bv[0] = 1.0; bv[1] = x - s->x0; bv[2] = 0.0; bv[3] = 0.0;
+        bd[0] = 0.0; bd[1] = 1.0; bd[2] = 0.0; bd[3] = 0.0;
+    } else if (x > x_end) {
+        double hh = s->h, e = x - x_end;
+        /* y_end = a + b h + c h^2 + d h^3, s_end = b + 2 c h + 3 d h^2 */
+        bv[0] = 1.0; bv[1] = hh + e; bv[2] = hh * hh + 2.0 * hh * e; bv[3] = hh * hh * hh + 3.0 * hh * hh * e;
+        bd[0] = 0.0; bd[1] = 1.0; bd[2] = 2.0 * hh; bd[3] = 3.0 * hh * hh;
+    } else {
+        bv[0] = 1.0; bv[1] = t; bv[2] = t * t; bv[3] = t * t * t;
+        bd[0] = 0.0; bd[1] = 1.0; bd[2] = 2.0 * t; bd[3] = 3.0 * t * t;
+    }
+}
+
+/* M: coefficients of the spline through unit knot vectors (end slopes 0):
+ * column q holds the 4(n-1) coefficients for y = e_q; row-major
+ * M[(4k + c) * n + q]. */
+int orc_spline_basis(int32_t n, double h, int32_t bc_lo, int32_t bc_hi, double *M)
+{
+    double *y = calloc((size_t)n, sizeof(double));
+    double *c = malloc(sizeof(double) * 4 * (size_t)(n - 1));
+    if (!y || !c) { free(y); free(c); return -2; }
+    for (int32_t q = 0; q < n; ++q) {
+        for (int32_t k = 0; k < n; ++k) y[k] = (k == q) ? 1.0 : 0.0;
+        int rc = orc_spline_coeffs(n, h, y, bc_lo, 0.0, bc_hi, 0.0, c);
+        if (rc) { free(y); free(c); return rc; }
+        for (int32_t r = 0; r < 4 * (n - 1); ++r) M[(size_t)r * n + q] = c[r];
+    }
+    free(y);
+    free(c);
+    return 0;
+}
+
+/* Loss of one configuration and dL/d(coefficients) of phi, f and F (arrays
+ * of 4(n-1) each, accumulated into: the caller zeroes them).  Returns the
+ * energy and forces through e_out / f_out when given. */
+int orc_force_match(const orc_pot *p, int64_t n, const double box[3], const double *pos,
+                    double e_ref, const double *f_ref, double w, double *loss,
+                    double *g_phi, double *g_f, double *g_F, double *e_out, double *f_out)
+{
+    if (p->ntypes != 1) return -1;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    double *wp = malloc(sizeof(double) * 3 * nn);
+    int32_t *types = calloc(nn, sizeof(int32_t));
+    int64_t *off = malloc(sizeof(int64_t) * (nn + 1));
+    double *rho = malloc(sizeof(double) * nn), *Fp = malloc(sizeof(double) * nn);
+    double *force = malloc(sizeof(double) * 3 * nn), *g = malloc(sizeof(double) * 3 * nn);
+    double *drho = calloc(nn, sizeof(double));
+    int64_t cap = 64 * (int64_t)nn;
+    int32_t *js = malloc(sizeof(int32_t) * (size_t)cap);
+    if (!wp || !types || !off || !rho || !Fp || !force || !g || !drho || !js) return -2;
+    memcpy(wp, pos, sizeof(double) * 3 * (size_t)n);
+    orc_wrap(n, box, wp);
+    int64_t m = orc_list_cells(n, box, p->r_cut + p->skin, wp, off, js, cap);
+    if (m < 0 || m > cap) return -3;
+    double energy[2], vir[6];
+    orc_eam_eval(p, n, box, wp, types, off, js, rho, Fp, force, energy, vir);
+    double E = energy[0] + energy[1];
+    double A = 2.0 * (E - e_ref) / (double)n;
+    double sq = 0.0;
+    for (int64_t i = 0; i < 3 * n; ++i) {
+        g[i] = force[i] - f_ref[i];
+        sq += g[i] * g[i];
+    }
+    *loss = (E - e_ref) * (E - e_ref) / (double)n + w * sq;
+    double rc2 = p->r_cut * p->r_cut;
+    const orc_spline *sphi = &p->phi[0], *sf = &p->f[0], *sF = &p->F[0];
+    /* drho_i = sum_j f'(r_ij) dr_ij */
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t q = off[i]; q < off[i + 1]; ++q) {
+            int64_t j = js[q];
+            double d[3];
+            double r2 = dist2(wp + 3 * i, wp + 3 * j, box, d);
+            if (!(r2 < rc2)) continue;
+            double r = sqrt(r2), df;
+            spl(sf, r, &df, NULL);
+            double dr = (d[0] * (g[3 * j] - g[3 * i]) + d[1] * (g[3 * j + 1] - g[3 * i + 1]) +
+                         d[2] * (g[3 * j + 2] - g[3 * i + 2])) / r;
+            drho[i] += df * dr;
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        double dF, d2F, bv[4], bd[4];
+        int64_t k;
+        spl(sF, rho[i], &dF, &d2F);
+        /* F: A B(rho_i) - 2w B'(rho_i) drho_i */
+        coef_rows(sF, rho[i], &k, bv, bd);
+        for (int c = 0; c < 4; ++c) g_F[4 * k + c] += A * bv[c] - 2.0 * w * bd[c] * drho[i];
+        for (int64_t q = off[i]; q < off[i + 1]; ++q) {
+            int64_t j = js[q];
+            double d[3];
+            double r2 = dist2(wp + 3 * i, wp + 3 * j, box, d);
+            if (!(r2 < rc2)) continue;
+            double r = sqrt(r2);
+            double dr = (d[0] * (g[3 * j] - g[3 * i]) + d[1] * (g[3 * j + 1] - g[3 * i + 1]) +
+                         d[2] * (g[3 * j + 2] - g[3 * i + 2])) / r;
+            /* phi: (1/2) A B(r) - w B'(r) dr */
+            coef_rows(sphi, r, &k, bv, bd);
+            for (int c = 0; c < 4; ++c) g_phi[4 * k + c] += 0.5 * A * bv[c] - w * bd[c] * dr;
+            /* f (density contributed by j at i):
+               A F'_i B(r) - 2w [F''_i drho_i B(r) + F'_i B'(r) dr] */
+            coef_rows(sf, r, &k, bv, bd);
+            for (int c = 0; c < 4; ++c)
+                g_f[4 * k + c] += A * dF * bv[c] - 2.0 * w * (d2F * drho[i] * bv[c] + dF * bd[c] * dr);
+        }
+    }
+    if (e_out) *e_out = E;
+    if (f_out) memcpy(f_out, force, sizeof(double) * 3 * (size_t)n);
+    free(wp); free(types); free(off); free(rho); free(Fp); free(force); free(g); free(drho); free(js);
+    return 0;
+}

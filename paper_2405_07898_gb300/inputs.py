@@ -298,3 +298,58 @@ def multi_type_system(cells=(6, 6, 6), seed: int = SEED_BASE + 50, n_knots: int 
     pot = Potential(mass=masses, F=[Fa, Fb], f=[fa, fb], phi=[phia, phiab, phib],
                     r_cut=pa.r_cut, skin=pa.skin)
     return System(box=box, pos=pos, vel=vel, types=types, pot=pot, label="bcc_alloy")
+
+
+# --------------------------------------------------------------------------
+# the force-matching workload (differentiation)
+
+
+def knot_potential(p: JohnsonParams, theta_phi, theta_f, theta_F, n_knots: int) -> Potential:
+    """A single-type potential whose phi, f and F are the cubic splines
+    through the given knot values on the same grids and end conditions as
+    `johnson_knots(p, n_knots)` (the clamped end slopes stay those of the
+    Johnson functions; they are not parameters)."""
+    F, f, phi = johnson_knots(p, n_knots)
+    phi = dataclasses.replace(phi, y=np.ascontiguousarray(theta_phi, dtype=np.float64))
+    f = dataclasses.replace(f, y=np.ascontiguousarray(theta_f, dtype=np.float64))
+    F = dataclasses.replace(F, y=np.ascontiguousarray(theta_F, dtype=np.float64))
+    return Potential(mass=np.array([p.mass]), F=[F], f=[f], phi=[phi], r_cut=p.r_cut, skin=p.skin)
+
+
+@dataclasses.dataclass
+class FitProblem:
+    """Force-matching problem: configurations (positions, box), the
+    parameter vector theta = (phi knots, f knots, F knots), and the weight w
+    of the force term.  References are computed by the caller with the
+    2,000-knot Johnson tables."""
+    params: JohnsonParams
+    n_knots: int
+    theta0: np.ndarray
+    configs: list
+    w: float
+
+    def potential(self, theta) -> Potential:
+        n = self.n_knots
+        return knot_potential(self.params, theta[:n], theta[n:2 * n], theta[2 * n:], n)
+
+
+def fit_problem(n_configs: int = 64, cells=(10, 10, 10), n_knots: int = 64, w: float = 0.1,
+                seed: int = SEED_BASE + 400) -> FitProblem:
+    """64 BCC configurations of 2,000 atoms with thermal displacements
+    sigma_c = 0.05 + 0.15 c/63 A, three of them (a seeded choice, ~5%) with
+    one vacancy; theta0 = the Johnson knots times (1 + 0.02 xi)."""
+    p = BCC_TA_LIKE
+    rng = np.random.Generator(np.random.PCG64(seed))
+    vac = set(rng.choice(n_configs, size=max(1, round(0.05 * n_configs)), replace=False).tolist())
+    configs = []
+    for c in range(n_configs):
+        pos, box = lattice(p, *cells)
+        sigma = 0.05 + 0.15 * c / max(n_configs - 1, 1)
+        pos = displace(pos, box, sigma, rng)
+        if c in vac:
+            pos = np.delete(pos, int(rng.integers(pos.shape[0])), axis=0)
+        configs.append((np.ascontiguousarray(pos), box))
+    F, f, phi = johnson_knots(p, n_knots)
+    theta = np.concatenate([phi.y, f.y, F.y])
+    noise = 1.0 + 0.02 * rng.normal(size=theta.shape)
+    return FitProblem(params=p, n_knots=n_knots, theta0=theta * noise, configs=configs, w=w)
