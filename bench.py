@@ -227,7 +227,8 @@ def run_ours(args):
                            "rebuild": prof["rebuild_ms"], "step": prof["step_ms"]},
             "whole_step_hbm_frac": ab["total"] * n * ts_per_s / world / 1e9 / peak,
             "clocks": clk,
-            "stats": {"rebuilds": st["rebuilds"], "max_neighbors": st["max_neighbors"]},
+            "stats": {"rebuilds": st["rebuilds"], "max_neighbors": st["max_neighbors"],
+                      "lanes_density": st["lanes_density"], "lanes_force": st["lanes_force"]},
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu

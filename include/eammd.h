@@ -101,14 +101,20 @@ enum { MD_PRECISION_FP64 = 0, MD_PRECISION_MIXED = 1 };
  *   use_graphs       1 = replay the step sequence as CUDA graphs with a
  *                    device-side conditional node for the list rebuild;
  *                    0 = launch kernels one by one (same kernels, same results).
- *   block_size       threads per block of the per-atom kernels (0 = 256). */
+ *   block_size       threads per block of the per-atom kernels (0 = 256).
+ *   lanes_per_atom   threads that share one atom's neighbour list in the
+ *                    density and force passes: 1, 2, 4 or 8; 0 = chosen at
+ *                    md_create by timing each (the choice is kept for the
+ *                    process, per precision and size class, so contexts of
+ *                    the same shape follow the same schedule).  Results
+ *                    depend on it only through FP summation order. */
 typedef struct {
     int32_t precision;
     int32_t rebuild_every;
     int32_t list_capacity;
     int32_t use_graphs;
     int32_t block_size;
-    int32_t reserved0;
+    int32_t lanes_per_atom;
     void *cuda_stream;
     void *(*alloc)(size_t bytes, void *alloc_ctx);
     void (*free)(void *ptr, void *alloc_ctx);
@@ -175,6 +181,8 @@ typedef struct {
     int32_t list_capacity;   /* list slots per atom */
     int64_t table_out_of_range; /* embedding lookups beyond the F table */
     int64_t kernel_launches; /* kernels queued by this context so far */
+    int32_t lanes_density;   /* lanes per atom of the density pass */
+    int32_t lanes_force;     /* lanes per atom of the force pass */
 } md_stats_t;
 
 md_status md_stats(md_ctx *ctx, md_stats_t *out);
@@ -192,6 +200,28 @@ typedef struct {
 } md_profile_t;
 
 md_status md_profile(md_ctx *ctx, int64_t nsteps, double dt, md_profile_t *out);
+
+/* Replace the spline values of the potential (the differentiation form: fit
+ * the splines of Section "Computational Molecular Dynamics" to reference
+ * data).  Every spline must keep its knot count, x0, dx and end conditions,
+ * and ntypes, masses, r_cut and skin must be unchanged.  Forces, energies and
+ * the virial of the current positions are re-evaluated.  Synchronises. */
+md_status md_set_potential(md_ctx *ctx, const md_potential *pot);
+
+/* Force-matching loss of the current configuration and its gradient with
+ * respect to the spline knot values (FP64 context, one atom type):
+ *   L = (E - e_ref)^2 / n + w sum_i |F_i - f_ref_i|^2,
+ * E the potential energy (Eq. 3) and F the forces (Eq. 4) of the current
+ * positions under the current splines.  f_ref: n*3 host array, original atom
+ * order.  grad (may be NULL): the derivative of L with respect to the knot
+ * values y[k] of phi[0], then f[0], then F[0], in that order (n_phi + n_f +
+ * n_F doubles, host memory); the clamped end slopes are not parameters.  The
+ * gradient includes the second-order terms through the forces: along
+ * g = F - f_ref it differentiates dE/dtheta (the density is recomputed, no
+ * per-pair term is stored).  Synchronises.  Errors: MD_ERR_ARG (wrong
+ * precision or several types), MD_ERR_CAPACITY (more than 200 KB of
+ * per-interval gradient bins, about 6,400 intervals in all). */
+md_status md_force_match(md_ctx *ctx, const double *f_ref, double e_ref, double w, double *loss, double *grad);
 
 /* Cell binning that allocates no device memory.  The paper has no
  * counterpart: this is a service for callers that cannot call cudaMalloc --
@@ -218,6 +248,55 @@ md_status md_profile(md_ctx *ctx, int64_t nsteps, double dt, md_profile_t *out);
  * same device) race and must be ordered by the caller. */
 md_status md_bin_cells_noalloc(const double box[3], double r_list, int64_t n, const double *d_pos,
                                int32_t *d_cell_start, int32_t *d_cell_atoms, void *cuda_stream);
+
+/* ---- batches: many independent systems in one persistent launch ----
+ * The batching form of the method: hundreds of periodic systems ("replicas")
+ * of uneven size, each with its own box and one-type potential, advanced
+ * together.  One thread block runs all phases of all steps of a replica
+ * (list rebuild, density, force and integration) with block-level barriers
+ * only; blocks take replicas largest first.  Mixed precision only (FP32
+ * pair arithmetic, FP64 positions, velocities and sums), the same
+ * arithmetic and list rules as a single context. */
+typedef struct md_batch md_batch;
+
+typedef struct {
+    int64_t n;             /* atoms, >= 1 */
+    double box[3];         /* each edge >= 3 (r_cut + skin) of its potential */
+    const double *pos;     /* n*3 Angstrom, caller order */
+    const double *vel;     /* n*3 Angstrom/fs or NULL */
+    int32_t potential;     /* index into the potentials of md_batch_create */
+    int32_t reserved;
+} md_replica;
+
+typedef struct {
+    int32_t replicas, blocks, threads_per_block, list_capacity;
+    int64_t atoms, steps, rebuilds, kernel_launches;
+    int32_t max_neighbors, reserved;
+} md_batch_info_t;
+
+/* pots: npot single-type potentials whose f and phi share a knot grid
+ * covering [0, r_cut].  opt: precision must be MD_PRECISION_MIXED;
+ * rebuild_every, list_capacity, use_graphs, cuda_stream and alloc/free
+ * apply.  Builds every replica's list and evaluates its initial forces and
+ * energies.  Synchronises. */
+md_status md_batch_create(int32_t nrep, const md_replica *reps, int32_t npot, const md_potential *pots,
+                          const md_options *opt, md_batch **out);
+
+/* nsteps velocity-Verlet steps of dt fs for every replica: one kernel launch
+ * (replayed from a captured graph when use_graphs).  Energies are evaluated
+ * at the last step.  Asynchronous. */
+md_status md_batch_step(md_batch *b, int64_t nsteps, double dt);
+
+/* pe[nrep], ke[nrep] (eV) of every replica; either may be NULL. */
+md_status md_batch_energy(md_batch *b, double *pe, double *ke);
+
+/* Positions, velocities and forces of replica r (n*3 each, caller order);
+ * any pointer may be NULL. */
+md_status md_batch_get_state(md_batch *b, int32_t r, double *pos, double *vel, double *force);
+
+md_status md_batch_info(md_batch *b, md_batch_info_t *out);
+const char *md_batch_last_error(const md_batch *b);
+void md_batch_destroy(md_batch *b);
 
 /* Message for the last failed call on ctx (or of md_create when ctx is NULL). */
 const char *md_last_error(const md_ctx *ctx);

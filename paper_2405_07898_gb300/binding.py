@@ -28,7 +28,9 @@ PRECISION = {"fp64": 0, "mixed": 1}
 # every entry point declared in include/eammd.h
 EXPORTS = ("md_options_default", "md_create", "md_step", "md_sync", "md_energy", "md_forces",
            "md_virial", "md_get_state", "md_set_state", "md_neighbors", "md_cells", "md_stats",
-           "md_profile", "md_last_error", "md_destroy", "md_bin_cells_noalloc")
+           "md_profile", "md_last_error", "md_destroy", "md_bin_cells_noalloc", "md_set_potential",
+           "md_force_match", "md_batch_create", "md_batch_step", "md_batch_energy", "md_batch_get_state",
+           "md_batch_info", "md_batch_last_error", "md_batch_destroy")
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -49,7 +51,7 @@ class PotentialC(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("rebuild_every", C.c_int32),
                 ("list_capacity", C.c_int32), ("use_graphs", C.c_int32),
-                ("block_size", C.c_int32), ("reserved0", C.c_int32),
+                ("block_size", C.c_int32), ("lanes_per_atom", C.c_int32),
                 ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p)]
 
@@ -57,13 +59,26 @@ class Options(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("rebuilds", C.c_int64), ("max_neighbors", C.c_int32),
                 ("list_capacity", C.c_int32), ("table_out_of_range", C.c_int64),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("lanes_density", C.c_int32),
+                ("lanes_force", C.c_int32)]
 
 
 class Profile(C.Structure):
     _fields_ = [("density_ms", C.c_double), ("force_ms", C.c_double), ("rebuild_ms", C.c_double),
                 ("step_ms", C.c_double), ("density_launches", C.c_int64),
                 ("force_launches", C.c_int64), ("rebuilds", C.c_int64)]
+
+
+class Replica(C.Structure):
+    _fields_ = [("n", C.c_int64), ("box", C.c_double * 3), ("pos", _dp), ("vel", _dp),
+                ("potential", C.c_int32), ("reserved", C.c_int32)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("replicas", C.c_int32), ("blocks", C.c_int32), ("threads_per_block", C.c_int32),
+                ("list_capacity", C.c_int32), ("atoms", C.c_int64), ("steps", C.c_int64),
+                ("rebuilds", C.c_int64), ("kernel_launches", C.c_int64), ("max_neighbors", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class MDError(RuntimeError):
@@ -122,6 +137,25 @@ def load(build_if_missing: bool = True):
     L.md_bin_cells_noalloc.argtypes = [_dp, C.c_double, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p]
     L.md_bin_cells_noalloc.restype = C.c_int
+    L.md_set_potential.argtypes = [C.c_void_p, C.POINTER(PotentialC)]
+    L.md_set_potential.restype = C.c_int
+    L.md_force_match.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp, _dp]
+    L.md_force_match.restype = C.c_int
+    L.md_batch_create.argtypes = [C.c_int32, C.POINTER(Replica), C.c_int32, C.POINTER(PotentialC),
+                                  C.POINTER(Options), C.POINTER(C.c_void_p)]
+    L.md_batch_create.restype = C.c_int
+    L.md_batch_step.argtypes = [C.c_void_p, C.c_int64, C.c_double]
+    L.md_batch_step.restype = C.c_int
+    L.md_batch_energy.argtypes = [C.c_void_p, _dp, _dp]
+    L.md_batch_energy.restype = C.c_int
+    L.md_batch_get_state.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.md_batch_get_state.restype = C.c_int
+    L.md_batch_info.argtypes = [C.c_void_p, C.POINTER(BatchInfo)]
+    L.md_batch_info.restype = C.c_int
+    L.md_batch_last_error.argtypes = [C.c_void_p]
+    L.md_batch_last_error.restype = C.c_char_p
+    L.md_batch_destroy.argtypes = [C.c_void_p]
+    L.md_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -179,7 +213,7 @@ class MD:
 
     def __init__(self, system, precision: str = "mixed", rebuild_every: int = 10,
                  list_capacity: int = 0, use_graphs: bool = True, block_size: int = 256,
-                 use_torch: bool | None = None):
+                 lanes_per_atom: int = 0, use_torch: bool | None = None):
         L = load()
         self._L = L
         self.n = int(system.n)
@@ -191,6 +225,7 @@ class MD:
         opt.list_capacity = list_capacity
         opt.use_graphs = 1 if use_graphs else 0
         opt.block_size = block_size
+        opt.lanes_per_atom = lanes_per_atom
         self._keep = []
         if use_torch is None:
             try:
@@ -207,19 +242,7 @@ class MD:
             opt.alloc, opt.free = a, f
             opt.cuda_stream = C.c_void_p(self.stream.cuda_stream)
         pot = system.pot
-
-        def splines(ks):
-            arr = (Spline * len(ks))()
-            for q, k in enumerate(ks):
-                y = _f64(k.y)
-                self._keep.append(y)
-                arr[q] = Spline(k.n, k.x0, k.dx, _d(y), k.bc_lo, k.bc_hi, k.d_lo, k.d_hi)
-            return arr
-
-        mass = _f64(pot.mass)
-        self._keep.append(mass)
-        pc = PotentialC(pot.ntypes, _d(mass), splines(pot.F), splines(pot.f), splines(pot.phi),
-                        pot.r_cut, pot.skin)
+        pc = self._potential_c(pot)
         box = _f64(system.box)
         pos = _f64(system.pos)
         vel = _f64(system.vel) if system.vel is not None else None
@@ -231,6 +254,45 @@ class MD:
             raise MDError(rc, L.md_last_error(None).decode())
         self.h = h
         self.box = box
+        self._pot = None
+
+    def _potential_c(self, pot):
+        keep = []
+
+        def splines(ks):
+            arr = (Spline * len(ks))()
+            for q, k in enumerate(ks):
+                y = _f64(k.y)
+                keep.append(y)
+                arr[q] = Spline(k.n, k.x0, k.dx, _d(y), k.bc_lo, k.bc_hi, k.d_lo, k.d_hi)
+            keep.append(arr)
+            return arr
+
+        mass = _f64(pot.mass)
+        keep.append(mass)
+        pc = PotentialC(pot.ntypes, _d(mass), splines(pot.F), splines(pot.f), splines(pot.phi),
+                        pot.r_cut, pot.skin)
+        self._keep.append(keep)
+        return pc
+
+    def set_potential(self, pot):
+        """md_set_potential: new spline values on the same grids."""
+        pc = self._potential_c(pot)
+        self._check(self._L.md_set_potential(self.h, C.byref(pc)))
+        self._keep.pop()
+        self._pot = pot
+
+    def force_match(self, f_ref, e_ref: float, w: float, grad: bool = True):
+        """md_force_match: (loss, knot gradient phi|f|F or None)."""
+        f_ref = _f64(f_ref)
+        loss = C.c_double()
+        g = None
+        if grad:
+            pot = self.system.pot if self._pot is None else self._pot
+            g = np.zeros(pot.phi[0].n + pot.f[0].n + pot.F[0].n)
+        self._check(self._L.md_force_match(self.h, _d(f_ref), float(e_ref), float(w), C.byref(loss),
+                                           _d(g) if g is not None else None))
+        return loss.value, g
 
     def _check(self, rc):
         if rc != MD_OK:
@@ -303,6 +365,110 @@ class MD:
     def close(self):
         if getattr(self, "h", None):
             self._L.md_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class MDBatch:
+    """Independent systems advanced together in one persistent launch
+    (md_batch_* of include/eammd.h).  `systems`: inputs.System objects with
+    one-type potentials; identical potentials are shared."""
+
+    def __init__(self, systems, rebuild_every: int = 10, list_capacity: int = 0, use_graphs: bool = True,
+                 use_torch: bool | None = None):
+        L = load()
+        self._L = L
+        self._keep = []
+        self.systems = list(systems)
+        pots, pot_index = [], []
+        for s in self.systems:
+            for q, p in enumerate(pots):
+                if p is s.pot:
+                    pot_index.append(q)
+                    break
+            else:
+                pots.append(s.pot)
+                pot_index.append(len(pots) - 1)
+        helper = MD.__new__(MD)
+        helper._keep = self._keep
+        pc = (PotentialC * len(pots))()
+        for q, p in enumerate(pots):
+            pc[q] = MD._potential_c(helper, p)
+        reps = (Replica * len(self.systems))()
+        for r, s in enumerate(self.systems):
+            pos = _f64(s.pos)
+            vel = _f64(s.vel) if s.vel is not None else None
+            self._keep += [pos, vel]
+            reps[r].n = s.n
+            for a in range(3):
+                reps[r].box[a] = float(s.box[a])
+            reps[r].pos = _d(pos)
+            reps[r].vel = _d(vel) if vel is not None else None
+            reps[r].potential = pot_index[r]
+        opt = Options()
+        L.md_options_default(C.byref(opt))
+        opt.precision = 1
+        opt.rebuild_every = rebuild_every
+        opt.list_capacity = list_capacity
+        opt.use_graphs = 1 if use_graphs else 0
+        if use_torch is None:
+            try:
+                import torch
+                use_torch = torch.cuda.is_available()
+            except Exception:
+                use_torch = False
+        if use_torch:
+            import torch
+            torch.cuda.init()
+            self.stream = torch.cuda.Stream()
+            a, f = _torch_allocator(self.stream)
+            self._keep += [a, f]
+            opt.alloc, opt.free = a, f
+            opt.cuda_stream = C.c_void_p(self.stream.cuda_stream)
+        h = C.c_void_p()
+        rc = L.md_batch_create(len(self.systems), reps, len(pots), pc, C.byref(opt), C.byref(h))
+        if rc != MD_OK:
+            raise MDError(rc, L.md_batch_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != MD_OK:
+            raise MDError(rc, self._L.md_batch_last_error(self.h).decode())
+
+    def step(self, nsteps: int, dt: float):
+        self._check(self._L.md_batch_step(self.h, int(nsteps), float(dt)))
+
+    def energy(self):
+        n = len(self.systems)
+        pe, ke = np.zeros(n), np.zeros(n)
+        self._check(self._L.md_batch_energy(self.h, _d(pe), _d(ke)))
+        return pe, ke
+
+    def get_state(self, r: int):
+        n = self.systems[r].n
+        pos, vel, force = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
+        self._check(self._L.md_batch_get_state(self.h, int(r), _ptr(pos), _ptr(vel), _ptr(force)))
+        return pos, vel, force
+
+    def info(self):
+        i = BatchInfo()
+        self._check(self._L.md_batch_info(self.h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in BatchInfo._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.md_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

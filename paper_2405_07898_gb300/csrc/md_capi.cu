@@ -4,6 +4,7 @@
 // marshalling of states between the caller's order and the sorted order.
 #include "eammd.h"
 #include "md_internal.cuh"
+#include "spline_host.h"
 
 #include <cuda_runtime.h>
 
@@ -11,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -21,52 +23,7 @@ namespace {
 
 thread_local std::string g_create_error;
 
-// --------------------------------------------------------------------------
-// Spline tables.  The C2 cubic through uniform knots is parametrised by its
-// knot slopes m_k: continuity of the second derivative at interior knots gives
-//   m_{k-1} + 4 m_k + m_{k+1} = 3 (y_{k+1} - y_{k-1}) / h,
-// a natural end gives 2 m_0 + m_1 = 3 (y_1 - y_0) / h (and its mirror), a
-// clamped end fixes the slope.  Each interval is the Hermite cubic through
-// (y_k, m_k) and (y_{k+1}, m_{k+1}).
-bool hermite_coefficients(const md_spline &s, std::vector<double> &rows)
-{
-    const int n = s.n;
-    const double h = s.dx;
-    const double *y = s.y;
-    std::vector<double> lo(n, 0.0), di(n, 0.0), up(n, 0.0), rhs(n, 0.0), m(n, 0.0);
-    if (s.bc_lo == 1) {
-        di[0] = 1.0; rhs[0] = s.d_lo;
-    } else {
-        di[0] = 2.0; up[0] = 1.0; rhs[0] = 3.0 * (y[1] - y[0]) / h;
-    }
-    for (int k = 1; k < n - 1; ++k) {
-        lo[k] = 1.0; di[k] = 4.0; up[k] = 1.0;
-        rhs[k] = 3.0 * (y[k + 1] - y[k - 1]) / h;
-    }
-    if (s.bc_hi == 1) {
-        di[n - 1] = 1.0; rhs[n - 1] = s.d_hi;
-    } else {
-        lo[n - 1] = 1.0; di[n - 1] = 2.0; rhs[n - 1] = 3.0 * (y[n - 1] - y[n - 2]) / h;
-    }
-    // tridiagonal solve (forward sweep, back substitution)
-    for (int k = 1; k < n; ++k) {
-        double w = lo[k] / di[k - 1];
-        di[k] -= w * up[k - 1];
-        rhs[k] -= w * rhs[k - 1];
-    }
-    m[n - 1] = rhs[n - 1] / di[n - 1];
-    for (int k = n - 2; k >= 0; --k) m[k] = (rhs[k] - up[k] * m[k + 1]) / di[k];
-    for (int k = 0; k < n - 1; ++k) {
-        double dy = (y[k + 1] - y[k]) / h;
-        rows.push_back(y[k]);
-        rows.push_back(m[k]);
-        rows.push_back((3.0 * dy - 2.0 * m[k] - m[k + 1]) / h);
-        rows.push_back((m[k] + m[k + 1] - 2.0 * dy) / (h * h));
-    }
-    for (double v : m)
-        if (!std::isfinite(v)) return false;
-    return true;
-}
+int blocks_for_host(int64_t n, int b) { return (int)((n + b - 1) / b); }
 
 template <class R>
 SplineDesc<R> make_desc(const md_spline &s, int offset, const double *row_last, const double *row0)
@@ -131,6 +88,15 @@ struct md_ctx {
     long long fixed_launches = 0;
     long long rebuilds_at_create = 0;
     int64_t host_steps = 0;       // step counter when n == 0
+    std::vector<md_spline> shapes; // grids of F[t], f[t], phi[q] (values not kept)
+    double r_cut = 0.0, skin = 0.0;
+    int off_F0 = 0, off_f0 = 0, off_phi0 = 0;  // coefficient rows of the type-0 tables
+    // force-matching adjoint workspace (FP64 path), allocated on first use
+    double *adj_g = nullptr, *adj_rho = nullptr, *adj_drho = nullptr, *adj_bins = nullptr, *adj_pg = nullptr;
+    double *adj_cg = nullptr, *adj_sq = nullptr, *adj_Mt = nullptr, *adj_kg = nullptr;
+    int *adj_knot_func = nullptr, *adj_func_coef0 = nullptr, *adj_func_ncoef = nullptr;
+    long long *adj_knot_mt0 = nullptr;
+    int adj_nrows = 0, adj_nknots = 0;
     std::string err;
 
     md_status fail(md_status s, const std::string &m)
@@ -190,7 +156,8 @@ template <>
 Bufs<double> &bufs<double>(md_ctx *ctx) { return ctx->Bd; }
 
 template <class R>
-bool alloc_buffers(md_ctx *ctx, const std::vector<double> &rows, const Tables<R> &tables)
+bool alloc_buffers(md_ctx *ctx, const std::vector<double> &rows, const std::vector<double> &rows2,
+                   const Tables<R> &tables)
 {
     using R4 = typename V4<R>::T;
     Bufs<R> &B = bufs<R>(ctx);
@@ -214,7 +181,6 @@ bool alloc_buffers(md_ctx *ctx, const std::vector<double> &rows, const Tables<R>
         ok = ok && alloc_n(ctx, B.type[s], n);
         ok = ok && alloc_n(ctx, B.shadow[s], n);
     }
-    ok = ok && alloc_n(ctx, B.Fp, n);
     ok = ok && alloc_n(ctx, B.cell, n);
     ok = ok && alloc_n(ctx, B.cell_old, n);
     ok = ok && alloc_n(ctx, B.slot, n);
@@ -223,22 +189,27 @@ bool alloc_buffers(md_ctx *ctx, const std::vector<double> &rows, const Tables<R>
     ok = ok && alloc_n(ctx, B.count, (size_t)G.ncells + 1);
     ok = ok && alloc_n(ctx, B.cell_start, (size_t)G.ncells + 1);
     ok = ok && alloc_n(ctx, B.block_sums, (size_t)(G.ncells + kScanBlock - 1) / kScanBlock + 1);
-    ok = ok && alloc_n(ctx, B.partials, (size_t)kEnergySlots * std::max(ctx->L.nblocks, 1));
+    ok = ok && alloc_n(ctx, B.partials, (size_t)kEnergySlots * std::max(ctx->L.pstride, 1));
     ok = ok && alloc_n(ctx, B.list, (size_t)ctx->L.cap * ctx->L.ld);
-    R4 *coef = nullptr;
+    R4 *coef = nullptr, *coef2 = nullptr;
     Tables<R> *tab = nullptr;
     ok = ok && alloc_n(ctx, coef, rows.size() / 4);
+    ok = ok && alloc_n(ctx, coef2, std::max<size_t>(rows2.size() / 4, 2));
     ok = ok && alloc_n(ctx, tab, 1);
     if (!ok) return false;
     B.coef = coef;
+    B.coef2 = coef2;
     B.tables = tab;
     B.st = ctx->st;
-    std::vector<R4> rr(rows.size() / 4);
-    for (size_t k = 0; k < rr.size(); ++k) {
-        R *dst = reinterpret_cast<R *>(&rr[k]);
-        for (int c = 0; c < 4; ++c) dst[c] = (R)rows[4 * k + c];
-    }
-    if (cudaMemcpy(coef, rr.data(), rr.size() * sizeof(R4), cudaMemcpyHostToDevice) != cudaSuccess) return false;
+    auto upload = [](R4 *dst_dev, const std::vector<double> &src) -> bool {
+        std::vector<R4> rr(src.size() / 4);
+        for (size_t k = 0; k < rr.size(); ++k) {
+            R *dst = reinterpret_cast<R *>(&rr[k]);
+            for (int c = 0; c < 4; ++c) dst[c] = (R)src[4 * k + c];
+        }
+        return rr.empty() || cudaMemcpy(dst_dev, rr.data(), rr.size() * sizeof(R4), cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    if (!upload(coef, rows) || !upload(coef2, rows2)) return false;
     if (cudaMemcpy(tab, &tables, sizeof(Tables<R>), cudaMemcpyHostToDevice) != cudaSuccess) return false;
     for (int a = 0; a < 3; ++a) {
         std::vector<double> c(G.ncell[a]);
@@ -563,13 +534,14 @@ md_status store_state(md_ctx *ctx, double *pos, double *vel, double *force)
     return MD_OK;
 }
 
+// Coefficient rows of all splines (F[t], f[t], phi[q] in that order), the
+// fused f | phi rows of the single-type fast path, and their descriptors.
 template <class R>
-md_status create_impl(md_ctx *ctx, const double *pos, const double *vel, const int32_t *types,
-                      const md_potential *pot)
+md_status build_tables(md_ctx *ctx, const md_potential *pot, std::vector<double> &rows, std::vector<double> &rows2,
+                       Tables<R> &tab)
 {
-    // spline tables: f[t], F[t], phi[q] appended into one coefficient array
-    std::vector<double> rows;
-    Tables<R> tab;
+    rows.clear();
+    rows2.clear();
     memset(&tab, 0, sizeof(tab));
     tab.ntypes = pot->ntypes;
     auto add = [&](const md_spline &s, SplineDesc<R> &d) -> bool {
@@ -585,17 +557,287 @@ md_status create_impl(md_ctx *ctx, const double *pos, const double *vel, const i
     }
     for (int q = 0; q < npair; ++q)
         if (!add(pot->phi[q], tab.phi[q])) return ctx->fail(MD_ERR_ARG, "spline system is singular");
+    // one type whose f and phi share a knot grid: interleave their rows so a
+    // pair's f' and phi' come from one 32-byte (FP32) row
+    const md_spline &f0 = pot->f[0], &p0 = pot->phi[0];
+    if (pot->ntypes == 1 && f0.n == p0.n && f0.x0 == p0.x0 && f0.dx == p0.dx) {
+        tab.fused = 1;
+        tab.fphi = tab.f[0];
+        tab.fphi.offset = 0;
+        for (int k = 0; k < f0.n - 1; ++k) {
+            for (int c = 0; c < 4; ++c) rows2.push_back(rows[4 * ((size_t)tab.f[0].offset + k) + c]);
+            for (int c = 0; c < 4; ++c) rows2.push_back(rows[4 * ((size_t)tab.phi[0].offset + k) + c]);
+        }
+    }
+    return MD_OK;
+}
+
+void set_lanes(md_ctx *ctx, int tpa_d, int tpa_f)
+{
+    Launch &L = ctx->L;
+    L.tpa_d = tpa_d;
+    L.tpa_f = tpa_f;
+    L.nb_d = blocks_for_host((int64_t)L.n * tpa_d, L.block);
+    L.nb_f = blocks_for_host((int64_t)L.n * tpa_f, L.block);
+}
+
+// Choices of the autotuner, per (precision, type path, size bucket), kept for
+// the life of the process so that every context of the same shape runs the
+// same schedule (and gives bitwise identical results).
+struct TuneKey {
+    int precision, multi, bucket;
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, std::pair<int, int>>> g_tune_cache;
+
+// Density and force (forces only, no integration) at the current state.
+template <class R>
+md_status reevaluate(md_ctx *ctx)
+{
+    const Bufs<R> &B = bufs<R>(ctx);
+    Launch L = ctx->L;
+    L.use_cond = 0;
+    ctx->fixed_launches += launch_density<R>(B, ctx->G, L, true);
+    ctx->fixed_launches += launch_force<R>(B, ctx->G, L, MODE_MEASURE, true);
+    ctx->fixed_launches += launch_reduce<R>(B, L);
+    CK(cudaGetLastError());
+    return MD_OK;
+}
+
+// Lanes per atom of the density and force passes: time each of 1, 2, 4, 8 on
+// the current state (density, and forces without integration; neither
+// changes positions or velocities) and keep the fastest of each.
+template <class R>
+md_status autotune(md_ctx *ctx)
+{
+    int bucket = 0;
+    for (int64_t m = ctx->n; m > 1; m >>= 1) ++bucket;
+    TuneKey key{ctx->precision, ctx->L.multi, bucket};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (auto &e : g_tune_cache)
+            if (e.first.precision == key.precision && e.first.multi == key.multi && e.first.bucket == key.bucket) {
+                set_lanes(ctx, e.second.first, e.second.second);
+                return reevaluate<R>(ctx);
+            }
+    }
+    const Bufs<R> &B = bufs<R>(ctx);
+    const int cand[4] = {1, 2, 4, 8};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_d = 1e30f, best_f = 1e30f;
+    int tpa_d = 1, tpa_f = 1;
+    const int reps = 4;
+    for (int c : cand) {
+        set_lanes(ctx, c, c);
+        Launch L = ctx->L;
+        L.use_cond = 0;
+        launch_density<R>(B, ctx->G, L, false);  // warm
+        CK(cudaEventRecord(e0, ctx->stream));
+        for (int r = 0; r < reps; ++r) launch_density<R>(B, ctx->G, L, false);
+        CK(cudaEventRecord(e1, ctx->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms_d = 0;
+        CK(cudaEventElapsedTime(&ms_d, e0, e1));
+        launch_force<R>(B, ctx->G, L, MODE_MEASURE, false);
+        CK(cudaEventRecord(e0, ctx->stream));
+        for (int r = 0; r < reps; ++r) launch_force<R>(B, ctx->G, L, MODE_MEASURE, false);
+        CK(cudaEventRecord(e1, ctx->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms_f = 0;
+        CK(cudaEventElapsedTime(&ms_f, e0, e1));
+        ctx->fixed_launches += 2 * (reps + 1);
+        if (ms_d < best_d) { best_d = ms_d; tpa_d = c; }
+        if (ms_f < best_f) { best_f = ms_f; tpa_f = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache.push_back({key, {tpa_d, tpa_f}});
+    }
+    set_lanes(ctx, tpa_d, tpa_f);
+    // forces and energies of the state under the chosen schedule
+    md_status rc = reevaluate<R>(ctx);
+    if (rc != MD_OK) return rc;
+    return check_device_errors(ctx);
+}
+
+
+// Replace the spline values of a context (same grids, same r_cut and skin)
+// and re-evaluate forces and energies at the current positions.
+template <class R>
+md_status set_potential_impl(md_ctx *ctx, const md_potential *pot)
+{
+    using R4 = typename V4<R>::T;
+    std::vector<double> rows, rows2;
+    Tables<R> tab;
+    md_status rc = build_tables<R>(ctx, pot, rows, rows2, tab);
+    if (rc != MD_OK) return rc;
+    Bufs<R> &B = bufs<R>(ctx);
+    auto upload = [&](const R4 *dst_dev, const std::vector<double> &src) -> cudaError_t {
+        std::vector<R4> rr(src.size() / 4);
+        for (size_t k = 0; k < rr.size(); ++k) {
+            R *dst = reinterpret_cast<R *>(&rr[k]);
+            for (int c = 0; c < 4; ++c) dst[c] = (R)src[4 * k + c];
+        }
+        if (rr.empty()) return cudaSuccess;
+        return cudaMemcpyAsync((void *)dst_dev, rr.data(), rr.size() * sizeof(R4), cudaMemcpyHostToDevice,
+                               ctx->stream);
+    };
+    CK(upload(B.coef, rows));
+    CK(upload(B.coef2, rows2));
+    CK(cudaMemcpyAsync((void *)B.tables, &tab, sizeof(Tables<R>), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));  // the host staging vectors go out of scope
+    if (ctx->n == 0) return MD_OK;
+    rc = reevaluate<R>(ctx);
+    if (rc != MD_OK) return rc;
+    return check_device_errors(ctx);
+}
+
+// Adjoint workspace and the transposed spline basis maps of phi, f, F.
+md_status adjoint_setup(md_ctx *ctx)
+{
+    if (ctx->adj_g) return MD_OK;
+    const size_t n = (size_t)ctx->n;
+    const md_spline *fs[3] = {&ctx->shapes[2], &ctx->shapes[1], &ctx->shapes[0]};  // phi, f, F
+    int nrows = 0, nknots = 0;
+    for (auto *sp : fs) {
+        nrows += sp->n - 1;
+        nknots += sp->n;
+    }
+    if (adjoint_smem_bytes(nrows) > 200 * 1024) return ctx->fail(MD_ERR_CAPACITY, "too many spline intervals for the adjoint bins");
+    std::vector<double> Mt;
+    std::vector<int> knot_func, coef0(3), ncoef(3);
+    std::vector<long long> mt0;
+    int coef_base = 0;
+    for (int fn = 0; fn < 3; ++fn) {
+        const md_spline &sp = *fs[fn];
+        coef0[fn] = coef_base;
+        ncoef[fn] = 4 * (sp.n - 1);
+        coef_base += ncoef[fn];
+        std::vector<double> y(sp.n, 0.0);
+        for (int q = 0; q < sp.n; ++q) {
+            std::fill(y.begin(), y.end(), 0.0);
+            y[q] = 1.0;
+            md_spline unit = sp;
+            unit.y = y.data();
+            unit.d_lo = 0.0;
+            unit.d_hi = 0.0;
+            std::vector<double> rows;
+            if (!hermite_coefficients(unit, rows)) return ctx->fail(MD_ERR_ARG, "spline basis failed");
+            knot_func.push_back(fn);
+            mt0.push_back((long long)Mt.size());
+            Mt.insert(Mt.end(), rows.begin(), rows.end());
+        }
+    }
+    const int nw = (int)((n + 31) / 32), nb = (int)((n + 255) / 256);
+    bool ok = alloc_n(ctx, ctx->adj_g, 3 * n) && alloc_n(ctx, ctx->adj_rho, n) && alloc_n(ctx, ctx->adj_drho, n) &&
+              alloc_n(ctx, ctx->adj_bins, (size_t)nw * 4 * nrows) && alloc_n(ctx, ctx->adj_pg, (size_t)nb) &&
+              alloc_n(ctx, ctx->adj_cg, (size_t)4 * nrows) && alloc_n(ctx, ctx->adj_sq, 1) &&
+              alloc_n(ctx, ctx->adj_Mt, Mt.size()) && alloc_n(ctx, ctx->adj_kg, (size_t)nknots) &&
+              alloc_n(ctx, ctx->adj_knot_func, (size_t)nknots) && alloc_n(ctx, ctx->adj_func_coef0, 3) &&
+              alloc_n(ctx, ctx->adj_func_ncoef, 3) && alloc_n(ctx, ctx->adj_knot_mt0, (size_t)nknots);
+    if (!ok) {
+        ctx->adj_g = nullptr;
+        return ctx->fail(MD_ERR_OOM, "adjoint workspace");
+    }
+    CK(cudaMemcpy(ctx->adj_Mt, Mt.data(), Mt.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->adj_knot_func, knot_func.data(), knot_func.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->adj_func_coef0, coef0.data(), 3 * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->adj_func_ncoef, ncoef.data(), 3 * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->adj_knot_mt0, mt0.data(), mt0.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    ctx->adj_nrows = nrows;
+    ctx->adj_nknots = nknots;
+    return MD_OK;
+}
+
+md_status force_match_impl(md_ctx *ctx, const double *f_ref, double e_ref, double w, double *loss, double *grad)
+{
+    md_status rc = check_device_errors(ctx);
+    if (rc != MD_OK) return rc;
+    const double E = ctx->st_host->e_embed + ctx->st_host->e_pair;
+    rc = adjoint_setup(ctx);
+    if (rc != MD_OK) return rc;
+    const size_t n = (size_t)ctx->n;
+    CK(cudaMemcpyAsync(ctx->stage, f_ref, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    const md_spline *fs[3] = {&ctx->shapes[2], &ctx->shapes[1], &ctx->shapes[0]};
+    AdjointArgs a;
+    memset(&a, 0, sizeof(a));
+    for (int q = 0; q < 3; ++q) {
+        a.x0[q] = fs[q]->x0;
+        a.h[q] = fs[q]->dx;
+        a.nint[q] = fs[q]->n - 1;
+    }
+    a.off_f = ctx->off_f0;
+    a.off_F = ctx->off_F0;
+    a.A = 2.0 * (E - e_ref) / (double)n;
+    a.w = w;
+    a.f_ref = ctx->stage;
+    a.g = ctx->adj_g;
+    a.rho = ctx->adj_rho;
+    a.drho = ctx->adj_drho;
+    a.block_bins = ctx->adj_bins;
+    a.partials_g = ctx->adj_pg;
+    a.coef_grad = ctx->adj_cg;
+    a.sq = ctx->adj_sq;
+    a.Mt = ctx->adj_Mt;
+    a.nknots_total = ctx->adj_nknots;
+    a.knot_func = ctx->adj_knot_func;
+    a.func_coef0 = ctx->adj_func_coef0;
+    a.func_ncoef = ctx->adj_func_ncoef;
+    a.knot_mt0 = ctx->adj_knot_mt0;
+    a.knot_grad = grad ? ctx->adj_kg : nullptr;
+    Launch L = ctx->L;
+    ctx->fixed_launches += launch_adjoint(ctx->Bd, ctx->G, L, a);
+    CK(cudaGetLastError());
+    double sq = 0.0;
+    CK(cudaMemcpyAsync(&sq, ctx->adj_sq, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (grad)
+        CK(cudaMemcpyAsync(grad, ctx->adj_kg, sizeof(double) * (size_t)ctx->adj_nknots, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (loss) *loss = (E - e_ref) * (E - e_ref) / (double)n + w * sq;
+    return MD_OK;
+}
+
+template <class R>
+md_status create_impl(md_ctx *ctx, const double *pos, const double *vel, const int32_t *types,
+                      const md_potential *pot)
+{
+    std::vector<double> rows, rows2;
+    Tables<R> tab;
+    md_status trc = build_tables<R>(ctx, pot, rows, rows2, tab);
+    if (trc != MD_OK) return trc;
+    ctx->L.multi = tab.fused ? 0 : 1;
+    ctx->shapes.clear();
+    for (int t = 0; t < pot->ntypes; ++t) ctx->shapes.push_back(pot->F[t]);
+    for (int t = 0; t < pot->ntypes; ++t) ctx->shapes.push_back(pot->f[t]);
+    for (int q = 0; q < pot->ntypes * (pot->ntypes + 1) / 2; ++q) ctx->shapes.push_back(pot->phi[q]);
+    for (auto &sh : ctx->shapes) sh.y = nullptr;
+    ctx->off_F0 = tab.F[0].offset;
+    ctx->off_f0 = tab.f[0].offset;
+    ctx->off_phi0 = tab.phi[0].offset;
+    ctx->r_cut = pot->r_cut;
+    ctx->skin = pot->skin;
 
     CK(cudaMallocHost((void **)&ctx->st_host, sizeof(DevState)));
     if (!alloc_n(ctx, ctx->st, 1) || !alloc_n(ctx, ctx->stage, 9 * (size_t)std::max<int64_t>(ctx->n, 1)) ||
         !alloc_n(ctx, ctx->types_orig, (size_t)std::max<int64_t>(ctx->n, 1)))
         return ctx->fail(MD_ERR_OOM, "device allocation failed");
-    if (!alloc_buffers<R>(ctx, rows, tab)) return ctx->fail(MD_ERR_OOM, "device allocation failed");
+    if (!alloc_buffers<R>(ctx, rows, rows2, tab)) return ctx->fail(MD_ERR_OOM, "device allocation failed");
     DevState h{};
     CK(cudaMemcpy(ctx->st, &h, sizeof(DevState), cudaMemcpyHostToDevice));
     if (ctx->n == 0) return MD_OK;
     CK(cudaMemcpy(ctx->types_orig, types, sizeof(int32_t) * (size_t)ctx->n, cudaMemcpyHostToDevice));
-    return load_and_measure<R>(ctx, pos, vel, 0);
+    md_status rc = load_and_measure<R>(ctx, pos, vel, 0);
+    if (rc != MD_OK) return rc;
+    if (ctx->opt.lanes_per_atom == 0) {
+        rc = autotune<R>(ctx);
+        if (rc != MD_OK) return rc;
+    }
+    return MD_OK;
 }
 
 }  // namespace
@@ -665,6 +907,9 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     if (o.block_size <= 0) o.block_size = 256;
     if (o.block_size > 256 || (o.block_size & 31)) return bad(MD_ERR_ARG, "block_size must be a multiple of 32, <= 256");
     if ((o.alloc == nullptr) != (o.free == nullptr)) return bad(MD_ERR_ARG, "alloc and free go together");
+    if (!(o.lanes_per_atom == 0 || o.lanes_per_atom == 1 || o.lanes_per_atom == 2 || o.lanes_per_atom == 4 ||
+          o.lanes_per_atom == 8))
+        return bad(MD_ERR_ARG, "lanes_per_atom must be 0 (tune), 1, 2, 4 or 8");
 
     md_ctx *ctx = new (std::nothrow) md_ctx();
     if (!ctx) return bad(MD_ERR_OOM, "host allocation failed");
@@ -707,12 +952,22 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     const double margin = 8.0 * (20.0 * hmax * r_list + 4.0 * r_list * r_list) * eps;
     G.screen_lo = G.rl2 - margin;
     G.screen_hi = G.rl2 + margin;
+    for (int a = 0; a < 3; ++a) G.h_f[a] = (float)G.h[a];
+    G.rc2_f = (float)G.rc2;
+    G.screen_lo_f = (float)G.screen_lo;
+    G.screen_hi_f = (float)G.screen_hi;
 
     Launch &L = ctx->L;
     L.n = (int)n;
     L.ld = (int)((n + 31) / 32 * 32);
     L.block = o.block_size;
     L.nblocks = (int)((n + L.block - 1) / L.block);
+    L.pstride = std::max(1, blocks_for_host(8 * n, L.block));
+    {
+        int lanes = o.lanes_per_atom > 0 ? o.lanes_per_atom : 4;
+        L.tpa_d = L.tpa_f = lanes;
+        L.nb_d = L.nb_f = blocks_for_host(n * lanes, L.block);
+    }
     L.ntypes = pot->ntypes;
     L.rebuild_every = o.rebuild_every;
     L.disp2_thr = 0.25 * pot->skin * pot->skin;
@@ -889,6 +1144,8 @@ md_status md_stats(md_ctx *ctx, md_stats_t *out)
     out->max_neighbors = h.max_nnb;
     out->table_out_of_range = (int64_t)h.table_oor;
     out->kernel_launches = ctx->fixed_launches + 8 * h.graph_rebuilds;
+    out->lanes_density = ctx->L.tpa_d;
+    out->lanes_force = ctx->L.tpa_f;
     return MD_OK;
 }
 
@@ -902,6 +1159,36 @@ md_status md_profile(md_ctx *ctx, int64_t nsteps, double dt, md_profile_t *out)
                                                         : profile_impl<double>(ctx, nsteps, dt, out);
     if (rc != MD_OK) return rc;
     return check_device_errors(ctx);
+}
+
+md_status md_set_potential(md_ctx *ctx, const md_potential *pot)
+{
+    if (!ctx || !pot) return ctx ? ctx->fail(MD_ERR_ARG, "pot is NULL") : MD_ERR_ARG;
+    if (pot->ntypes != ctx->ntypes || pot->r_cut != ctx->r_cut || pot->skin != ctx->skin || !pot->mass ||
+        !pot->F || !pot->f || !pot->phi)
+        return ctx->fail(MD_ERR_ARG, "md_set_potential keeps ntypes, r_cut and skin");
+    std::vector<const md_spline *> given;
+    for (int t = 0; t < pot->ntypes; ++t) given.push_back(&pot->F[t]);
+    for (int t = 0; t < pot->ntypes; ++t) given.push_back(&pot->f[t]);
+    for (int q = 0; q < pot->ntypes * (pot->ntypes + 1) / 2; ++q) given.push_back(&pot->phi[q]);
+    for (size_t k = 0; k < given.size(); ++k) {
+        const md_spline &a = *given[k], &b = ctx->shapes[k];
+        if (!spline_ok(a) || a.n != b.n || a.x0 != b.x0 || a.dx != b.dx || a.bc_lo != b.bc_lo || a.bc_hi != b.bc_hi)
+            return ctx->fail(MD_ERR_ARG, "md_set_potential keeps every knot grid and end condition");
+    }
+    for (int t = 0; t < pot->ntypes; ++t)
+        if (pot->mass[t] != ctx->mass[t]) return ctx->fail(MD_ERR_ARG, "md_set_potential keeps the masses");
+    return ctx->precision == MD_PRECISION_MIXED ? set_potential_impl<float>(ctx, pot)
+                                                : set_potential_impl<double>(ctx, pot);
+}
+
+md_status md_force_match(md_ctx *ctx, const double *f_ref, double e_ref, double w, double *loss, double *grad)
+{
+    if (!ctx || !f_ref) return ctx ? ctx->fail(MD_ERR_ARG, "f_ref is NULL") : MD_ERR_ARG;
+    if (ctx->precision != MD_PRECISION_FP64 || ctx->ntypes != 1 || ctx->n < 1)
+        return ctx->fail(MD_ERR_ARG, "md_force_match needs an FP64 context with one atom type and n >= 1");
+    if (!std::isfinite(e_ref) || !std::isfinite(w)) return ctx->fail(MD_ERR_ARG, "e_ref and w must be finite");
+    return force_match_impl(ctx, f_ref, e_ref, w, loss, grad);
 }
 
 const char *md_last_error(const md_ctx *ctx)

@@ -8,9 +8,10 @@
 //   v[set][3]    FP64 SoA, velocities
 //   id[set], type[set]   int32: original index and atom type
 //   uref[3]      R SoA, xr minus the centre of the atom's cell (|uref| <= h/2)
-//   shadow[2]    R4 (u_x, u_y, u_z, 0), u = uref + d: the coordinates the pair
-//                kernels read; double-buffered across steps
-//   Fp           R, embedding derivative F'(rho_i) of the current step
+//   shadow[2]    R4 (u_x, u_y, u_z, F'), u = uref + d: the coordinates the pair
+//                kernels read, and the embedding derivative F'(rho_i) that the
+//                density pass stores for the force pass; double-buffered
+//                across steps
 //   fcache[3]    R SoA, forces of the last closed step
 //   list         uint32 [capacity][ld] (column k of atom i at k*ld + i):
 //                neighbour index in bits 0..26, stencil code in bits 27..31
@@ -71,6 +72,8 @@ struct SplineDesc {
 template <class R>
 struct Tables {
     int ntypes;
+    int fused;             // 1: one type whose f and phi share a knot grid (fphi)
+    SplineDesc<R> fphi;    // grid of the fused rows: coef2[2k] = f, coef2[2k+1] = phi
     SplineDesc<R> F[kMaxTypes], f[kMaxTypes], phi[kMaxPairs];
 };
 
@@ -85,6 +88,10 @@ struct Geom {
     double screen_lo;    // candidates with r2 below this are in the list for sure
     double screen_hi;    // ... above this are out for sure; in between: exact FP64 test
     double rc2;          // r_cut^2
+    // the same in FP32, so that FP32 kernels convert nothing on the FP64 pipe
+    float h_f[3];
+    float rc2_f;
+    float screen_lo_f, screen_hi_f;
 };
 
 template <class R>
@@ -97,7 +104,6 @@ struct Bufs {
     int *type[2];
     R *uref[3];
     R4 *shadow[2];
-    R *Fp;
     R *fcache[3];
     int *cell;
     double *center[3];   // cell centres per axis, (c + 1/2) h_d
@@ -117,6 +123,7 @@ struct Bufs {
     // state and tables
     DevState *st;
     const R4 *coef;
+    const R4 *coef2;     // fused f | phi rows (single-type fast path)
     const Tables<R> *tables;
 };
 
@@ -126,6 +133,12 @@ struct Launch {
     int cap;        // list slots per atom
     int block;      // threads per block of per-atom kernels
     int nblocks;    // ceil(n / block)
+    int tpa_d;      // lanes per atom of the density pass (1, 2, 4, 8)
+    int tpa_f;      // lanes per atom of the force pass
+    int nb_d;       // blocks of the density pass
+    int nb_f;       // blocks of the force pass
+    int pstride;    // stride between energy slots in partials (>= nb_d, nb_f)
+    int multi;      // general type-dependent path (several types or unfused tables)
     int ntypes;
     int rebuild_every;
     double disp2_thr;                 // (skin/2)^2
@@ -151,5 +164,28 @@ template <class R>
 int launch_load_state(const Bufs<R> &B, const Launch &L, const double *pos, const double *vel, const int *types);
 template <class R>
 int launch_store_state(const Bufs<R> &B, const Launch &L, double *pos, double *vel, double *force);
+
+// Adjoint of the force-matching loss for one configuration (adjoint.cu).
+// All buffers are device memory owned by the context.
+struct AdjointArgs {
+    double x0[3], h[3];
+    int nint[3];
+    int off_f, off_F;       // coefficient offsets of f and F in B.coef
+    double A, w;
+    const double *f_ref;    // n*3, caller order (device)
+    double *g, *rho, *drho; // 3n, n, n
+    double *block_bins;     // nblocks_warp * 4 * nrows
+    double *partials_g;     // >= blocks of k_adj_g
+    double *coef_grad;      // 4 * nrows
+    double *sq;             // 1
+    const double *Mt;       // transposed basis matrices
+    int nknots_total;
+    const int *knot_func, *func_coef0, *func_ncoef;
+    const long long *knot_mt0;
+    double *knot_grad;      // nknots_total (nullptr: skip the knot map)
+};
+
+int launch_adjoint(const Bufs<double> &B, const Geom &G, const Launch &L, const AdjointArgs &a);
+size_t adjoint_smem_bytes(int nrows);
 
 }  // namespace eammd

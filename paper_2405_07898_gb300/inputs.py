@@ -353,3 +353,33 @@ def fit_problem(n_configs: int = 64, cells=(10, 10, 10), n_knots: int = 64, w: f
     theta = np.concatenate([phi.y, f.y, F.y])
     noise = 1.0 + 0.02 * rng.normal(size=theta.shape)
     return FitProblem(params=p, n_knots=n_knots, theta0=theta * noise, configs=configs, w=w)
+
+
+# --------------------------------------------------------------------------
+# the batched workload
+
+
+def _near_box(cells_wanted: int, min_cells: int):
+    nx = max(min_cells, int(round(cells_wanted ** (1.0 / 3.0))))
+    ny = max(min_cells, int(round((cells_wanted / nx) ** 0.5)))
+    nz = max(min_cells, int(round(cells_wanted / (nx * ny))))
+    return nx, ny, nz
+
+
+def replica_batch(nrep: int = 512, n_min: int = 1024, n_max: int = 16384, seed: int = SEED_BASE):
+    """Independent periodic systems of uneven size: target atom counts
+    log-uniform in [n_min, n_max], realised as the nearest orthorhombic
+    lattice with at least 3 list radii per edge; the first half BCC (a = 3.30),
+    the second half FCC (a = 3.615, Cu-like); temperatures uniform in
+    [200, 1200] K; replica r uses seed + r."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = np.exp(rng.uniform(np.log(n_min), np.log(n_max), size=nrep))
+    temps = rng.uniform(200.0, 1200.0, size=nrep)
+    out = []
+    for r in range(nrep):
+        p = BCC_TA_LIKE if r < nrep // 2 else FCC_CU_LIKE
+        per_cell = 2 if p.lattice == "bcc" else 4
+        min_cells = int(math.ceil(3.0 * (p.r_cut + p.skin) / p.a))
+        cells = _near_box(max(1, int(round(sizes[r] / per_cell))), min_cells)
+        out.append(thermal_system(p, cells, 0.02, float(temps[r]), seed + r, label=f"rep{r}"))
+    return out

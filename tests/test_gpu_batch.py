@@ -1,0 +1,92 @@
+"""The batching form: many independent replicas (BCC and FCC, uneven sizes,
+different temperatures) advanced in one persistent launch, through the C ABI,
+against the oracle replica by replica."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2405_07898_gb300 import binding, inputs as I
+
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 2e-5
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def small_batch():
+    return [
+        I.thermal_system(I.BCC_TA_LIKE, (5, 5, 5), 0.02, 300.0, 101),
+        I.thermal_system(I.FCC_CU_LIKE, (5, 5, 5), 0.02, 900.0, 102),
+        I.thermal_system(I.BCC_TA_LIKE, (9, 7, 6), 0.03, 1200.0, 103),
+        I.thermal_system(I.FCC_CU_LIKE, (7, 6, 5), 0.02, 200.0, 104),
+        I.thermal_system(I.BCC_TA_LIKE, (12, 12, 12), 0.02, 600.0, 105),
+        I.thermal_system(I.FCC_CU_LIKE, (10, 9, 8), 0.02, 450.0, 106),
+        I.thermal_system(I.BCC_TA_LIKE, (6, 5, 5), 0.02, 300.0, 107),
+    ]
+
+
+def oracle_state(s, pos=None):
+    pot = O.Potential(s.pot)
+    p = s.pos if pos is None else pos
+    return O.eam_eval(pot, O.wrap(p, s.box), s.box, s.types)
+
+
+def test_initial_forces_and_energies_per_replica():
+    systems = small_batch()
+    with binding.MDBatch(systems) as b:
+        pe, ke = b.energy()
+        for r, s in enumerate(systems):
+            _, _, F, E, _ = oracle_state(s)
+            _, _, f = b.get_state(r)
+            assert rel(f, F) < MIXED_TOL, r
+            assert abs(pe[r] - E.sum()) / abs(E.sum()) < MIXED_TOL
+            m = s.pot.mass[0]
+            ke_ref = 0.5 * m * (s.vel**2).sum() / I.ACCEL_EV_A_AMU
+            assert abs(ke[r] - ke_ref) / ke_ref < 1e-9
+
+
+def test_trajectories_against_oracle():
+    systems = small_batch()
+    with binding.MDBatch(systems) as b:
+        b.step(40, 2.0)
+        pe, ke = b.energy()
+        info = b.info()
+        assert info["steps"] == 40 and info["rebuilds"] >= 4 * len(systems)
+        for r, s in enumerate(systems):
+            ref = O.System(O.Potential(s.pot), s.box, s.pos, s.vel, s.types)
+            ref.step(40, 2.0)
+            st = ref.state()
+            pos, vel, f = b.get_state(r)
+            d = pos - st["pos"]
+            d -= s.box * np.round(d / s.box)
+            assert np.abs(d).max() < 1e-4, r
+            ope, oke = ref.energy()
+            assert abs((pe[r] + ke[r]) - (ope + oke)) / abs(ope + oke) < 1e-5, r
+            # forces at the batch's own positions
+            _, _, F, _, _ = oracle_state(s, pos)
+            assert rel(f, F) < MIXED_TOL, r
+
+
+def test_batch_equals_itself_and_graphs_equal_plain_launches():
+    systems = small_batch()[:4]
+    runs = []
+    for use_graphs in (True, False):
+        with binding.MDBatch(systems, use_graphs=use_graphs) as b:
+            b.step(25, 2.0)
+            b.step(25, 2.0)
+            runs.append([b.get_state(r) for r in range(len(systems))] + [b.energy()])
+    for (a, c) in zip(runs[0][:-1], runs[1][:-1]):
+        for x, y in zip(a, c):
+            np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(runs[0][-1][0], runs[1][-1][0])
+
+
+def test_rejects_bad_replicas():
+    s = I.bcc_2000_fp64()
+    tiny = I.System(box=s.box / 3, pos=s.pos / 3, vel=s.vel, types=s.types, pot=s.pot)
+    with pytest.raises(binding.MDError) as e:
+        binding.MDBatch([s, tiny])
+    assert e.value.status == -2
