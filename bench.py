@@ -133,9 +133,13 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    system = I.bcc_799496()
+    if args.cells:
+        system = I.thermal_system(I.BCC_TA_LIKE, tuple(args.cells), 0.02, 300.0, I.SEED_BASE + 3,
+                                  label="bcc_%dx%dx%d" % tuple(args.cells))
+    else:
+        system = I.bcc_799496()
     n = system.n
-    md = binding.MD(system, precision=args.precision, rebuild_every=10, use_graphs=True)
+    md = binding.MD(system, precision=args.precision, rebuild_every=10, use_graphs=not args.eager)
     stream = md.stream
 
     def bench_step():
@@ -161,10 +165,9 @@ def run_ours(args):
     clk = clocks.stop()
     ms_total = e0.elapsed_time(e1)
     if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        from paper_2405_07898_gb300 import sharding
+        ms_total = sharding.reduce_max(ms_total, device="cuda")
         torch.distributed.barrier()
-        ms_total = float(t.item())
     launches = md.stats()["kernel_launches"] - launches0
     ms_per_step = ms_total / args.steps
     ts_per_s = world * args.steps * MD_STEPS_PER_BENCH_STEP / (ms_total * 1e-3)
@@ -209,11 +212,12 @@ def run_ours(args):
             "vs_baseline": None,
             "dtype": "f32+f64",
             "data": "synthetic: seeded BCC lattice, Gaussian displacements, Maxwell velocities",
-            "config": {"workload": WORKLOAD, "atoms": n, "md_steps_per_step": MD_STEPS_PER_BENCH_STEP,
+            "config": {"workload": WORKLOAD if not args.cells else system.label + "_mixed", "atoms": n, "md_steps_per_step": MD_STEPS_PER_BENCH_STEP,
                        "dt_fs": DT_FS, "rebuild_every": 10, "precision": args.precision,
                        "list": "full Verlet list, r_list 4.8 A, 26 entries/atom",
                        "l2": "working set ~0.35 GB > L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
+                       "launch": "eager" if args.eager else "cuda graphs",
                        "atom_steps_per_s": ts_per_s * n},
             "e2e": {"value": e2e_value, "unit": "timesteps/s",
                     "h2d_bytes_per_step": 2 * 3 * n * 8, "d2h_bytes_per_step": 16},
@@ -228,13 +232,99 @@ def run_ours(args):
             "whole_step_hbm_frac": ab["total"] * n * ts_per_s / world / 1e9 / peak,
             "clocks": clk,
             "stats": {"rebuilds": st["rebuilds"], "max_neighbors": st["max_neighbors"],
-                      "lanes_density": st["lanes_density"], "lanes_force": st["lanes_force"]},
+                      "lanes_density": st["lanes_density"], "lanes_force": st["lanes_force"],
+                      "rows_density": st["rows_density"], "rows_force": st["rows_force"]},
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _timed_steps(md, nsteps, dt, reps=1):
+    import torch
+    md.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(md.stream)
+    for _ in range(reps):
+        md.step(nsteps, dt)
+    e1.record(md.stream)
+    md.sync()
+    return e0.elapsed_time(e1) * 1e-3
+
+
+def run_sweep(args):
+    """Strong-scaling sweep: BCC cubes of 1,024 .. 314,928 atoms and the
+    799,496-atom box at 1,000 K (mixed precision): timesteps/s of the graph
+    path, and for systems that fit one thread block's schedule (<= 20,000
+    atoms) of the persistent single-replica path."""
+    import torch
+    from paper_2405_07898_gb300 import binding, inputs as I
+
+    torch.cuda.set_device(0)
+    rows = []
+    for s in I.sweep_systems(temperature=1000.0):
+        md = binding.MD(s, precision="mixed")
+        steps = max(200, min(20000, int(2e8 // s.n) // 10 * 10))
+        md.step(100, DT_FS)
+        t = _timed_steps(md, steps, DT_FS)
+        row = {"atoms": s.n, "steps": steps, "graph_ts_per_s": steps / t,
+               "graph_atom_steps_per_s": s.n * steps / t}
+        md.close()
+        if s.n <= 20000:
+            b = binding.MDBatch([s])
+            b.step(100, DT_FS)
+            b.energy()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(b.stream)
+            b.step(steps, DT_FS)
+            e1.record(b.stream)
+            b.energy()
+            tb = e0.elapsed_time(e1) * 1e-3
+            row["persistent_ts_per_s"] = steps / tb
+            b.close()
+        rows.append(row)
+    print(json.dumps({"workload": "bcc_sweep_1000K_mixed", "unit": "timesteps/s", "sweep": rows}), flush=True)
+
+
+def run_drift(args):
+    """NVE energy drift: the 250,000-atom Sigma-5 bicrystal at 1,000 K and the
+    799,496-atom box at 300 K, mixed precision, dt = 2 fs; total energy
+    sampled every 100 steps; drift = least-squares slope per atom scaled to
+    1e5 steps."""
+    import numpy as np
+    import torch
+    from paper_2405_07898_gb300 import binding, inputs as I
+
+    torch.cuda.set_device(0)
+    out = []
+    cases = [(I.sigma5_bicrystal(temperature=1000.0), args.drift_steps),
+             (I.bcc_799496(), max(args.drift_steps // 10, 1000))]
+    for s, nsteps in cases:
+        for precision in ("mixed",) if s.n > 300000 else ("mixed", "fp64"):
+            if precision == "fp64" and nsteps > 20000:
+                nsteps_p = 20000
+            else:
+                nsteps_p = nsteps
+            md = binding.MD(s, precision=precision)
+            e = [sum(md.energy())]
+            t0 = time.perf_counter()
+            for _ in range(nsteps_p // 100):
+                md.step(100, DT_FS)
+                e.append(sum(md.energy()))
+            wall = time.perf_counter() - t0
+            e = np.array(e) / s.n
+            steps = np.arange(len(e)) * 100.0
+            slope = np.polyfit(steps, e, 1)[0]
+            out.append({"system": s.label, "atoms": s.n, "precision": precision, "steps": nsteps_p,
+                        "drift_ev_per_atom_per_1e5_steps": float(slope * 1e5),
+                        "max_abs_dev_ev_per_atom": float(np.abs(e - e[0]).max()),
+                        "ts_per_s_with_sampling": nsteps_p / wall})
+            md.close()
+    print(json.dumps({"workload": "nve_drift", "runs": out}), flush=True)
 
 
 def load_traffic():
@@ -319,11 +409,24 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="bcc_799496", choices=["bcc_799496", "sweep", "drift"],
+                    help="bcc_799496: the benchmark line; sweep / drift: the strong-scaling sweep and the "
+                         "NVE drift runs (their own JSON lines)")
+    ap.add_argument("--drift-steps", type=int, default=100000)
+    ap.add_argument("--cells", type=int, nargs=3, default=None,
+                    help="BCC cells per axis of a smaller profiling case (default: the 74x74x73 workload)")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch the step kernels one by one instead of replaying CUDA graphs "
+                         "(same kernels; lets a profiler list every launch)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
+    elif args.workload == "drift":
+        run_drift(args)
     else:
         run_ours(args)
 

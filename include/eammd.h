@@ -82,6 +82,7 @@ typedef struct {
 } md_potential;
 
 enum { MD_PRECISION_FP64 = 0, MD_PRECISION_MIXED = 1 };
+enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2 };
 
 /* Options.  Fill with md_options_default() and change what you need.
  *   precision        MD_PRECISION_FP64: all arithmetic in FP64.
@@ -107,7 +108,25 @@ enum { MD_PRECISION_FP64 = 0, MD_PRECISION_MIXED = 1 };
  *                    md_create by timing each (the choice is kept for the
  *                    process, per precision and size class, so contexts of
  *                    the same shape follow the same schedule).  Results
- *                    depend on it only through FP summation order. */
+ *                    depend on it only through FP summation order.
+ *   schedule         MD_SCHEDULE_AUTO (0): chosen with lanes_per_atom when
+ *                    that is 0 (timed), else MD_SCHEDULE_ATOMS.
+ *                    MD_SCHEDULE_ATOMS: the density and force passes run one
+ *                    atom per lanes_per_atom threads, neighbour records
+ *                    gathered from device memory.
+ *                    MD_SCHEDULE_ROWS: one block per row of cells (fixed y,
+ *                    z cell index) stages the records of the 3 x 3 rows
+ *                    around it in shared memory and gathers from there
+ *                    (lanes_per_atom 1, 2 or 4).  Applies to one atom type
+ *                    whose f and phi share a knot grid; otherwise, and for
+ *                    any block whose rows outgrow the stage sized at
+ *                    md_create, the atom-parallel gathers are used.  Forces
+ *                    are bitwise those of MD_SCHEDULE_ATOMS with the same
+ *                    lanes_per_atom; energy sums differ in rounding only.
+ *   stage_capacity   records a row-staged block holds; 0 = 1.1 x the most
+ *                    that any 3 x 3 block of rows holds at md_create, + 32.
+ *                    Must fit the shared memory of a block (160 KB of
+ *                    16-byte (mixed) or 32-byte (fp64) records). */
 typedef struct {
     int32_t precision;
     int32_t rebuild_every;
@@ -119,6 +138,8 @@ typedef struct {
     void *(*alloc)(size_t bytes, void *alloc_ctx);
     void (*free)(void *ptr, void *alloc_ctx);
     void *alloc_ctx;
+    int32_t schedule;
+    int32_t stage_capacity;
 } md_options;
 
 void md_options_default(md_options *opt);
@@ -183,6 +204,10 @@ typedef struct {
     int64_t kernel_launches; /* kernels queued by this context so far */
     int32_t lanes_density;   /* lanes per atom of the density pass */
     int32_t lanes_force;     /* lanes per atom of the force pass */
+    int32_t rows_density;    /* 1: density pass row-staged (MD_SCHEDULE_ROWS) */
+    int32_t rows_force;      /* 1: force pass row-staged */
+    int32_t stage_capacity;  /* records a row-staged block holds (0: none) */
+    int32_t reserved;
 } md_stats_t;
 
 md_status md_stats(md_ctx *ctx, md_stats_t *out);

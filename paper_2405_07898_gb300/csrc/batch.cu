@@ -27,8 +27,7 @@
 namespace eammd {
 namespace {
 
-constexpr int kBatchBlock = 512;
-constexpr int kBatchWarps = kBatchBlock / 32;
+constexpr int kMaxBatchWarps = 16;  // blocks of up to 512 threads
 
 struct RepParam {
     int n;          // atoms
@@ -84,15 +83,16 @@ enum { BATCH_INIT = 0, BATCH_RUN = 1 };
 struct Smem {
     RepParam P;
     float4 shift[27];
-    double red_d[kBatchWarps];
-    float red_f[kBatchWarps];
+    double red_d[kMaxBatchWarps];
+    float red_f[kMaxBatchWarps];
     int red_i[32];
     int carry;
     int need;
     int rep;
-    float4 cell_u[kBatchWarps][32];
-    int cell_cnt[kBatchWarps][32];
+    float4 cell_u[kMaxBatchWarps][32];
 };
+
+__device__ __forceinline__ int nwarps() { return (int)(blockDim.x >> 5); }
 
 __device__ __forceinline__ float block_max_f(float v, Smem &S)
 {
@@ -101,7 +101,7 @@ __device__ __forceinline__ float block_max_f(float v, Smem &S)
     if ((threadIdx.x & 31) == 0) S.red_f[threadIdx.x >> 5] = v;
     __syncthreads();
     float m = 0.f;
-    for (int w = 0; w < kBatchWarps; ++w) m = fmaxf(m, S.red_f[w]);
+    for (int w = 0; w < nwarps(); ++w) m = fmaxf(m, S.red_f[w]);
     __syncthreads();
     return m;
 }
@@ -113,7 +113,7 @@ __device__ __forceinline__ int block_max_i(int v, Smem &S)
     if ((threadIdx.x & 31) == 0) S.red_i[threadIdx.x >> 5] = v;
     __syncthreads();
     int m = 0;
-    for (int w = 0; w < kBatchWarps; ++w) m = max(m, S.red_i[w]);
+    for (int w = 0; w < nwarps(); ++w) m = max(m, S.red_i[w]);
     __syncthreads();
     return m;
 }
@@ -127,7 +127,7 @@ __device__ __forceinline__ double block_sum_ff(float hi, float lo, Smem &S)
     if ((threadIdx.x & 31) == 0) S.red_d[threadIdx.x >> 5] = s;
     __syncthreads();
     double t = 0.0;
-    for (int w = 0; w < kBatchWarps; ++w) t += S.red_d[w];
+    for (int w = 0; w < nwarps(); ++w) t += S.red_d[w];
     __syncthreads();
     return t;
 }
@@ -183,14 +183,14 @@ __device__ void rb_scan(const BatchBufs &B, const RepParam &P, Smem &S)
         if (lane == 31) S.red_i[warp] = incl;
         __syncthreads();
         if (warp == 0) {
-            const int w = (lane < kBatchWarps) ? S.red_i[lane] : 0;
+            const int w = (lane < nwarps()) ? S.red_i[lane] : 0;
             int wi = w;
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, wi, o);
                 if (lane >= o) wi += y;
             }
             S.red_i[lane] = wi - w;  // exclusive prefix of the warp totals
-            if (lane == 31) S.red_i[31] = wi;  // chunk total (kBatchWarps <= 31)
+            if (lane == 31) S.red_i[31] = wi;  // chunk total (at most 16 warps)
         }
         __syncthreads();
         const int excl = S.carry + S.red_i[warp] + incl - v;
@@ -285,7 +285,7 @@ __device__ void rb_list(const BatchBufs &B, Smem &S, int set, int sp, int cap, R
     const float4 *sw = B.shadow[sp] + P.atom_off;
     const unsigned lt = (1u << lane) - 1u;
     int my_max = 0;
-    for (int c = warp; c < P.ncells; c += kBatchWarps) {
+    for (int c = warp; c < P.ncells; c += nwarps()) {
         const int cx = c % P.ncell[0], cy = (c / P.ncell[0]) % P.ncell[1], cz = c / (P.ncell[0] * P.ncell[1]);
         int e_start = 0, e_cnt = 0;
         if (lane < 27) {
@@ -307,10 +307,8 @@ __device__ void rb_list(const BatchBufs &B, Smem &S, int set, int sp, int cap, R
         const int a0 = B.cell_start[P.cs_off + c], na = B.cell_start[P.cs_off + c + 1] - a0;
         for (int base = 0; base < na; base += 32) {
             const int nb = min(32, na - base);
-            if (lane < nb) {
-                W.cell_u[warp][lane] = sw[a0 + base + lane];
-                W.cell_cnt[warp][lane] = 0;
-            }
+            if (lane < nb) W.cell_u[warp][lane] = sw[a0 + base + lane];
+            int my_cnt = 0;
             __syncwarp();
             for (int m0 = 0; m0 < total; m0 += 32) {
                 const int m = m0 + lane;
@@ -343,22 +341,19 @@ __device__ void rb_list(const BatchBufs &B, Smem &S, int set, int sp, int cap, R
                                  : ((r2 > P.screen_hi_f) ? false : rb_exact(B, P, set, P.atom_off + p, P.atom_off + q));
                     }
                     const unsigned mask = __ballot_sync(0xffffffffu, in);
-                    const int cnt0 = W.cell_cnt[warp][a];
+                    const int cnt0 = __shfl_sync(0xffffffffu, my_cnt, a);
                     if (in) {
                         const int pos = cnt0 + __popc(mask & lt);
                         if (pos < cap)
                             B.list[P.list_off + (size_t)pos * P.ld + p] = (uint32_t)q | ((uint32_t)code << kCodeShift);
                     }
-                    __syncwarp();
-                    if (lane == 0) W.cell_cnt[warp][a] = cnt0 + __popc(mask);
-                    __syncwarp();
+                    if (lane == a) my_cnt += __popc(mask);
                 }
             }
             if (lane < nb) {
-                const int cnt = W.cell_cnt[warp][lane];
-                B.nnb[P.atom_off + a0 + base + lane] = min(cnt, cap);
-                if (cnt > cap) atomicOr(&st->error, ERR_LIST_OVERFLOW);
-                my_max = max(my_max, cnt);
+                B.nnb[P.atom_off + a0 + base + lane] = min(my_cnt, cap);
+                if (my_cnt > cap) atomicOr(&st->error, ERR_LIST_OVERFLOW);
+                my_max = max(my_max, my_cnt);
             }
             __syncwarp();
         }
@@ -539,7 +534,8 @@ __device__ void run_replica(const BatchBufs &B, Smem &S, int r, int mode, int ns
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kBatchBlock) k_batch(BatchBufs B, int mode, int nsteps, double dt)
+template <int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) k_batch(BatchBufs B, int mode, int nsteps, double dt)
 {
     __shared__ Smem S;
     for (;;) {
@@ -619,6 +615,7 @@ struct md_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int grid = 0;
+    int schedule = 0;
     double *stage = nullptr;
     int max_n = 0;
     long long launches = 0;
@@ -663,10 +660,20 @@ bool balloc_n(md_batch *b, T *&p, size_t count)
                            std::string(#call) + ": " + cudaGetErrorString(e_));                    \
     } while (0)
 
+// schedules the autotuner chooses from: threads per block, blocks per SM
+struct BatchSchedule {
+    int block, min_blocks;
+};
+constexpr BatchSchedule kSchedules[3] = {{512, 1}, {256, 2}, {256, 3}};
+
 md_status batch_launch(md_batch *b, int mode, int nsteps, double dt)
 {
     BCK(cudaMemsetAsync(b->B.queue, 0, sizeof(int), b->stream));
-    k_batch<<<b->grid, kBatchBlock, 0, b->stream>>>(b->B, mode, nsteps, dt);
+    switch (b->schedule) {
+    case 1: k_batch<256, 2><<<b->grid, 256, 0, b->stream>>>(b->B, mode, nsteps, dt); break;
+    case 2: k_batch<256, 3><<<b->grid, 256, 0, b->stream>>>(b->B, mode, nsteps, dt); break;
+    default: k_batch<512, 1><<<b->grid, 512, 0, b->stream>>>(b->B, mode, nsteps, dt); break;
+    }
     b->launches += 1;
     BCK(cudaGetLastError());
     return MD_OK;
@@ -889,12 +896,65 @@ md_status md_batch_create(int32_t nrep, const md_replica *reps, int32_t npot, co
     B.nrep = nrep;
     B.cap = cap;
     B.rebuild_every = o.rebuild_every;
-    int per_sm = 1, sms = 1, dev = 0;
+    int sms = 1, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBatchBlock, 0);
-    b->grid = std::max(1, std::min(nrep, std::max(per_sm, 1) * sms));
+    auto grid_for = [&](int sched) {
+        int per_sm = 1;
+        if (sched == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<256, 2>, 256, 0);
+        else if (sched == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<256, 3>, 256, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<512, 1>, 512, 0);
+        return std::max(1, std::min(nrep, std::max(per_sm, 1) * sms));
+    };
+    b->schedule = 0;
+    b->grid = grid_for(0);
     md_status rc = batch_launch(b, BATCH_INIT, 1, 0.0);
+    if (rc == MD_OK) rc = batch_sync(b);
+    // schedule autotuner: right after the initial build every replica is
+    // rebuild_every steps from its next build, so rebuild_every - 1 steps of
+    // dt = 0 change nothing but the counters, which are restored afterwards
+    if (rc == MD_OK && o.rebuild_every > 1 && o.lanes_per_atom == 0) {
+        const int trial = std::min(o.rebuild_every - 1, 8);
+        float best = 1e30f;
+        int best_s = 0;
+        cudaEvent_t t0, t1;
+        cudaEventCreate(&t0);
+        cudaEventCreate(&t1);
+        for (int round = 0; round < 2 && rc == MD_OK; ++round)
+            for (int sc = 0; sc < 3 && rc == MD_OK; ++sc) {
+                b->schedule = sc;
+                b->grid = grid_for(sc);
+                cudaEventRecord(t0, b->stream);
+                rc = batch_launch(b, BATCH_RUN, trial, 0.0);
+                cudaEventRecord(t1, b->stream);
+                if (rc == MD_OK) rc = batch_sync(b);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, t0, t1);
+                if (round == 1 && ms < best) {
+                    best = ms;
+                    best_s = sc;
+                }
+                if (rc == MD_OK && cudaMemcpy(B.st, b->st_host, sizeof(RepState) * nrep, cudaMemcpyHostToDevice) != cudaSuccess)
+                    rc = MD_ERR_CUDA;
+                if (rc == MD_OK) {
+                    // restore the counters of the state after the initial build
+                    std::vector<RepState> restore(nrep);
+                    memcpy(restore.data(), b->st_host, sizeof(RepState) * nrep);
+                    for (int r = 0; r < nrep; ++r) {
+                        restore[r].step -= trial;
+                        restore[r].since_build -= trial;
+                        if (trial & 1) restore[r].sp ^= 1;
+                    }
+                    if (cudaMemcpy(B.st, restore.data(), sizeof(RepState) * nrep, cudaMemcpyHostToDevice) != cudaSuccess)
+                        rc = MD_ERR_CUDA;
+                }
+            }
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        b->schedule = best_s;
+        b->grid = grid_for(best_s);
+        b->launches = 1;
+    }
     if (rc == MD_OK) rc = batch_sync(b);
     if (rc != MD_OK) {
         g_batch_create_error = b->err;
@@ -983,7 +1043,7 @@ md_status md_batch_info(md_batch *b, md_batch_info_t *out)
     out->replicas = b->nrep;
     out->atoms = b->total;
     out->blocks = b->grid;
-    out->threads_per_block = kBatchBlock;
+    out->threads_per_block = kSchedules[b->schedule].block;
     out->list_capacity = b->B.cap;
     out->kernel_launches = b->launches;
     for (int r = 0; r < b->nrep; ++r) {

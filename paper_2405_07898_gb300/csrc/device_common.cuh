@@ -174,13 +174,12 @@ __device__ __forceinline__ void block_sums_t(const T (&v)[NV], double *partials,
         if (lane == 0) sm[warp][k] = s;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += sm[w][k];
-            partials[(size_t)(slot0 + k) * stride + blockIdx.x] = s;
-        }
+    // lane k of warp 0 adds value k over the warps, in warp order
+    if (threadIdx.x < NV) {
+        const int k = threadIdx.x;
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += sm[w][k];
+        partials[(size_t)(slot0 + k) * stride + blockIdx.x] = s;
     }
 }
 

@@ -572,13 +572,15 @@ md_status build_tables(md_ctx *ctx, const md_potential *pot, std::vector<double>
     return MD_OK;
 }
 
-void set_lanes(md_ctx *ctx, int tpa_d, int tpa_f)
+void set_lanes(md_ctx *ctx, int tpa_d, int tpa_f, int rows_d, int rows_f)
 {
     Launch &L = ctx->L;
     L.tpa_d = tpa_d;
     L.tpa_f = tpa_f;
-    L.nb_d = blocks_for_host((int64_t)L.n * tpa_d, L.block);
-    L.nb_f = blocks_for_host((int64_t)L.n * tpa_f, L.block);
+    L.staged_d = rows_d;
+    L.staged_f = rows_f;
+    L.nb_d = rows_d ? L.nrows : blocks_for_host((int64_t)L.n * tpa_d, L.block);
+    L.nb_f = rows_f ? L.nrows : blocks_for_host((int64_t)L.n * tpa_f, L.block);
 }
 
 // Choices of the autotuner, per (precision, type path, size bucket), kept for
@@ -587,8 +589,56 @@ void set_lanes(md_ctx *ctx, int tpa_d, int tpa_f)
 struct TuneKey {
     int precision, multi, bucket;
 };
+struct TuneChoice {
+    int tpa_d, tpa_f, rows_d, rows_f;
+};
 std::mutex g_tune_mu;
-std::vector<std::pair<TuneKey, std::pair<int, int>>> g_tune_cache;
+std::vector<std::pair<TuneKey, TuneChoice>> g_tune_cache;
+
+// Largest dynamic shared memory of a row-staged block.  The attribute only
+// permits it; occupancy follows what a launch asks for.
+constexpr int kStageLimitBytes = 160 * 1024;
+
+// Stage capacity of the row-staged passes from the cell occupancy of the
+// current list build: the most records any 3 x 3 block of rows holds, with
+// room for atoms that change cells at later builds.  Blocks that outgrow it
+// gather from device memory.  0 when rows staging does not apply.
+template <class R>
+md_status setup_staging(md_ctx *ctx)
+{
+    Launch &L = ctx->L;
+    L.stage_cap = 0;
+    const md_options &o = ctx->opt;
+    const bool wanted = o.schedule == MD_SCHEDULE_ROWS || (o.schedule == MD_SCHEDULE_AUTO && o.lanes_per_atom == 0);
+    if (L.multi || !wanted || ctx->n == 0) return MD_OK;
+    const Geom &G = ctx->G;
+    const int nx = G.ncell[0], ny = G.ncell[1], nz = G.ncell[2];
+    std::vector<int> cs((size_t)G.ncells + 1);
+    CK(cudaMemcpyAsync(cs.data(), bufs<R>(ctx).cell_start, sizeof(int) * cs.size(), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    int64_t most = 0;
+    for (int cz = 0; cz < nz; ++cz)
+        for (int cy = 0; cy < ny; ++cy) {
+            int64_t sum = 0;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int ey = (cy + dy + ny) % ny, ez = (cz + dz + nz) % nz;
+                    const int r = ez * ny + ey;
+                    sum += cs[(size_t)(r + 1) * nx] - cs[(size_t)r * nx];
+                }
+            most = std::max(most, sum);
+        }
+    const int64_t cap = o.stage_capacity > 0 ? (int64_t)o.stage_capacity
+                                             : ((int64_t)std::ceil(1.1 * (double)most) + 32 + 31) / 32 * 32;
+    if (cap * (int64_t)sizeof(typename V4<R>::T) > kStageLimitBytes) {
+        if (o.stage_capacity > 0) return ctx->fail(MD_ERR_ARG, "stage_capacity exceeds the shared memory of a block");
+        return MD_OK;
+    }
+    CK(allow_row_staging<R>(kStageLimitBytes));
+    L.stage_cap = (int)cap;
+    return MD_OK;
+}
 
 // Density and force (forces only, no integration) at the current state.
 template <class R>
@@ -604,9 +654,11 @@ md_status reevaluate(md_ctx *ctx)
     return MD_OK;
 }
 
-// Lanes per atom of the density and force passes: time each of 1, 2, 4, 8 on
-// the current state (density, and forces without integration; neither
-// changes positions or velocities) and keep the fastest of each.
+// Schedule of the density and force passes: time the atom-parallel passes
+// with 1, 2, 4, 8 lanes per atom and, where a stage was sized, the
+// row-staged passes with 1, 2, 4, on the current state (density, and forces
+// without integration; neither changes positions or velocities) and keep the
+// fastest of each.
 template <class R>
 md_status autotune(md_ctx *ctx)
 {
@@ -617,53 +669,68 @@ md_status autotune(md_ctx *ctx)
         std::lock_guard<std::mutex> lock(g_tune_mu);
         for (auto &e : g_tune_cache)
             if (e.first.precision == key.precision && e.first.multi == key.multi && e.first.bucket == key.bucket) {
-                set_lanes(ctx, e.second.first, e.second.second);
+                const TuneChoice &c = e.second;
+                const bool ok = ctx->L.stage_cap > 0 || (!c.rows_d && !c.rows_f);
+                set_lanes(ctx, c.tpa_d, c.tpa_f, ok && c.rows_d, ok && c.rows_f);
                 return reevaluate<R>(ctx);
             }
     }
     const Bufs<R> &B = bufs<R>(ctx);
-    const int cand[4] = {1, 2, 4, 8};
+    struct Cand {
+        int tpa, rows;
+    };
+    std::vector<Cand> cand = {{1, 0}, {2, 0}, {4, 0}, {8, 0}};
+    if (ctx->L.stage_cap > 0) cand.insert(cand.end(), {{1, 1}, {2, 1}, {4, 1}});
+    const int nc = (int)cand.size();
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    float best_d = 1e30f, best_f = 1e30f;
-    int tpa_d = 1, tpa_f = 1;
-    const int reps = 4;
-    for (int c : cand) {
-        set_lanes(ctx, c, c);
-        Launch L = ctx->L;
-        L.use_cond = 0;
-        launch_density<R>(B, ctx->G, L, false);  // warm
-        CK(cudaEventRecord(e0, ctx->stream));
-        for (int r = 0; r < reps; ++r) launch_density<R>(B, ctx->G, L, false);
-        CK(cudaEventRecord(e1, ctx->stream));
-        CK(cudaEventSynchronize(e1));
-        float ms_d = 0;
-        CK(cudaEventElapsedTime(&ms_d, e0, e1));
-        launch_force<R>(B, ctx->G, L, MODE_MEASURE, false);
-        CK(cudaEventRecord(e0, ctx->stream));
-        for (int r = 0; r < reps; ++r) launch_force<R>(B, ctx->G, L, MODE_MEASURE, false);
-        CK(cudaEventRecord(e1, ctx->stream));
-        CK(cudaEventSynchronize(e1));
-        float ms_f = 0;
-        CK(cudaEventElapsedTime(&ms_f, e0, e1));
-        ctx->fixed_launches += 2 * (reps + 1);
-        if (ms_d < best_d) { best_d = ms_d; tpa_d = c; }
-        if (ms_f < best_f) { best_f = ms_f; tpa_f = c; }
+    // rounds over the candidates in turn (so clock and cache drift hit all
+    // alike); each candidate keeps its fastest single launch
+    std::vector<float> best_d(nc, 1e30f), best_f(nc, 1e30f);
+    const int rounds = 6;
+    for (int round = 0; round < rounds; ++round) {
+        for (int ci = 0; ci < nc; ++ci) {
+            set_lanes(ctx, cand[ci].tpa, cand[ci].tpa, cand[ci].rows, cand[ci].rows);
+            Launch L = ctx->L;
+            L.use_cond = 0;
+            float ms = 0;
+            CK(cudaEventRecord(e0, ctx->stream));
+            launch_density<R>(B, ctx->G, L, false);
+            CK(cudaEventRecord(e1, ctx->stream));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaGetLastError());
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (round > 0) best_d[ci] = std::min(best_d[ci], ms);
+            CK(cudaEventRecord(e0, ctx->stream));
+            launch_force<R>(B, ctx->G, L, MODE_MEASURE, false);
+            CK(cudaEventRecord(e1, ctx->stream));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaGetLastError());
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (round > 0) best_f[ci] = std::min(best_f[ci], ms);
+            ctx->fixed_launches += 2;
+        }
+    }
+    // candidates in order of preference: a later one must win by 3%
+    int cd = 0, cf = 0;
+    for (int ci = 1; ci < nc; ++ci) {
+        if (best_d[ci] < 0.97f * best_d[cd]) cd = ci;
+        if (best_f[ci] < 0.97f * best_f[cf]) cf = ci;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    const TuneChoice choice{cand[cd].tpa, cand[cf].tpa, cand[cd].rows, cand[cf].rows};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune_cache.push_back({key, {tpa_d, tpa_f}});
+        g_tune_cache.push_back({key, choice});
     }
-    set_lanes(ctx, tpa_d, tpa_f);
+    set_lanes(ctx, choice.tpa_d, choice.tpa_f, choice.rows_d, choice.rows_f);
     // forces and energies of the state under the chosen schedule
     md_status rc = reevaluate<R>(ctx);
     if (rc != MD_OK) return rc;
     return check_device_errors(ctx);
 }
-
 
 // Replace the spline values of a context (same grids, same r_cut and skin)
 // and re-evaluate forces and energies at the current positions.
@@ -833,10 +900,17 @@ md_status create_impl(md_ctx *ctx, const double *pos, const double *vel, const i
     CK(cudaMemcpy(ctx->types_orig, types, sizeof(int32_t) * (size_t)ctx->n, cudaMemcpyHostToDevice));
     md_status rc = load_and_measure<R>(ctx, pos, vel, 0);
     if (rc != MD_OK) return rc;
-    if (ctx->opt.lanes_per_atom == 0) {
-        rc = autotune<R>(ctx);
+    rc = setup_staging<R>(ctx);
+    if (rc != MD_OK) return rc;
+    const md_options &o = ctx->opt;
+    if (o.schedule == MD_SCHEDULE_ROWS && !ctx->L.multi) {
+        const int lanes = o.lanes_per_atom > 0 ? o.lanes_per_atom : 2;
+        set_lanes(ctx, lanes, lanes, 1, 1);
+        rc = reevaluate<R>(ctx);
         if (rc != MD_OK) return rc;
+        return check_device_errors(ctx);
     }
+    if (o.lanes_per_atom == 0 && o.schedule == MD_SCHEDULE_AUTO) return autotune<R>(ctx);
     return MD_OK;
 }
 
@@ -910,6 +984,11 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     if (!(o.lanes_per_atom == 0 || o.lanes_per_atom == 1 || o.lanes_per_atom == 2 || o.lanes_per_atom == 4 ||
           o.lanes_per_atom == 8))
         return bad(MD_ERR_ARG, "lanes_per_atom must be 0 (tune), 1, 2, 4 or 8");
+    if (o.schedule < MD_SCHEDULE_AUTO || o.schedule > MD_SCHEDULE_ROWS)
+        return bad(MD_ERR_ARG, "schedule must be MD_SCHEDULE_AUTO, _ATOMS or _ROWS");
+    if (o.schedule == MD_SCHEDULE_ROWS && o.lanes_per_atom == 8)
+        return bad(MD_ERR_ARG, "row-staged passes take 1, 2 or 4 lanes per atom");
+    if (o.stage_capacity < 0) return bad(MD_ERR_ARG, "stage_capacity must be >= 0");
 
     md_ctx *ctx = new (std::nothrow) md_ctx();
     if (!ctx) return bad(MD_ERR_OOM, "host allocation failed");
@@ -962,7 +1041,8 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     L.ld = (int)((n + 31) / 32 * 32);
     L.block = o.block_size;
     L.nblocks = (int)((n + L.block - 1) / L.block);
-    L.pstride = std::max(1, blocks_for_host(8 * n, L.block));
+    L.nrows = G.ncell[1] * G.ncell[2];
+    L.pstride = std::max({1, blocks_for_host(8 * n, L.block), L.nrows});
     {
         int lanes = o.lanes_per_atom > 0 ? o.lanes_per_atom : 4;
         L.tpa_d = L.tpa_f = lanes;
@@ -1146,6 +1226,10 @@ md_status md_stats(md_ctx *ctx, md_stats_t *out)
     out->kernel_launches = ctx->fixed_launches + 8 * h.graph_rebuilds;
     out->lanes_density = ctx->L.tpa_d;
     out->lanes_force = ctx->L.tpa_f;
+    out->rows_density = ctx->L.staged_d;
+    out->rows_force = ctx->L.staged_f;
+    out->stage_capacity = ctx->L.stage_cap;
+    out->reserved = 0;
     return MD_OK;
 }
 

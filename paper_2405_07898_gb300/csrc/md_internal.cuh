@@ -137,7 +137,11 @@ struct Launch {
     int tpa_f;      // lanes per atom of the force pass
     int nb_d;       // blocks of the density pass
     int nb_f;       // blocks of the force pass
-    int pstride;    // stride between energy slots in partials (>= nb_d, nb_f)
+    int pstride;    // stride between energy slots in partials (>= nb_d, nb_f, nrows)
+    int nrows;      // rows of cells (ncell[1] * ncell[2]): blocks of a row-staged pass
+    int stage_cap;  // neighbour records one row-staged block stages (0: none)
+    int staged_d;   // density pass row-staged
+    int staged_f;   // force pass row-staged
     int multi;      // general type-dependent path (several types or unfused tables)
     int ntypes;
     int rebuild_every;
@@ -152,13 +156,15 @@ struct Launch {
 
 enum StepMode { MODE_MEASURE = 0, MODE_CLOSE = 1, MODE_CLOSE_OPEN = 2 };
 
-// Host-side launchers (kernels.cu).  All are asynchronous on L.stream and
+// Host-side launchers (rebuild.cu, pair_f32.cu, pair_f64.cu).  All are asynchronous on L.stream and
 // return the number of kernels queued.
 template <class R> int launch_rebuild(const Bufs<R> &B, const Geom &G, const Launch &L);
 template <class R> int launch_decide(const Bufs<R> &B, const Launch &L);
 template <class R> int launch_open(const Bufs<R> &B, const Geom &G, const Launch &L);
 template <class R> int launch_density(const Bufs<R> &B, const Geom &G, const Launch &L, bool energy);
 template <class R> int launch_force(const Bufs<R> &B, const Geom &G, const Launch &L, int mode, bool energy);
+// Opt the row-staged passes in to `bytes` of dynamic shared memory.
+template <class R> cudaError_t allow_row_staging(int bytes);
 template <class R> int launch_reduce(const Bufs<R> &B, const Launch &L);
 template <class R>
 int launch_load_state(const Bufs<R> &B, const Launch &L, const double *pos, const double *vel, const int *types);

@@ -4,4 +4,5 @@
 namespace eammd {
 template int launch_density<float>(const Bufs<float> &, const Geom &, const Launch &, bool);
 template int launch_force<float>(const Bufs<float> &, const Geom &, const Launch &, int, bool);
+template cudaError_t allow_row_staging<float>(int);
 }  // namespace eammd

@@ -214,44 +214,54 @@ __device__ __forceinline__ bool exact_in_list(const double *const xr[3], int p, 
 // stencil order, ascending id inside a cell) closer than r_list.  The test
 // runs in R on the cell-centred coordinates; candidates within the rounding
 // margin of r_list are decided by exact_in_list, so the list is bit-identical
-// to the FP64 definition.
+// to the FP64 definition.  The stencil loop is unrolled: cell codes and
+// shifts are constants of each unrolled iteration.
 template <class R>
-__global__ void k_build_list(Bufs<R> B, Geom G, int n, int ld, int cap)
+__global__ void __launch_bounds__(256) k_build_list(Bufs<R> B, Geom G, int n, int ld, int cap)
 {
     using R4 = typename V4<R>::T;
-    __shared__ R4 sh[27];
     DevState *st = B.st;
     if (!st->need_rebuild) return;
-    fill_shift<R>(sh, G);
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
     int cnt = 0;
     if (p < n) {
         const int sp = st->sp, s = st->set;
         const double *const xr[3] = {B.xr[s][0], B.xr[s][1], B.xr[s][2]};
         const R4 *sw = B.shadow[sp];
         const R lo = g_screen_lo<R>(G), hi = g_screen_hi<R>(G);
-        int cell = B.cell[p];
-        int cx = cell % G.ncell[0], cy = (cell / G.ncell[0]) % G.ncell[1], cz = cell / (G.ncell[0] * G.ncell[1]);
-        R4 up = sw[p];
-        for (int code = 0; code < 27; ++code) {
-            int ex = cx + code % 3 - 1, ey = cy + (code / 3) % 3 - 1, ez = cz + code / 9 - 1;
-            ex += (ex < 0) ? G.ncell[0] : ((ex >= G.ncell[0]) ? -G.ncell[0] : 0);
-            ey += (ey < 0) ? G.ncell[1] : ((ey >= G.ncell[1]) ? -G.ncell[1] : 0);
-            ez += (ez < 0) ? G.ncell[2] : ((ez >= G.ncell[2]) ? -G.ncell[2] : 0);
-            int e = (ez * G.ncell[1] + ey) * G.ncell[0] + ex;
-            R4 shf = sh[code];
-            int q1 = B.cell_start[e + 1];
-            for (int q = B.cell_start[e]; q < q1; ++q) {
-                if (q == p) continue;
-                R4 uq = sw[q];
-                R dx = (uq.x - up.x) + shf.x;
-                R dy = (uq.y - up.y) + shf.y;
-                R dz = (uq.z - up.z) + shf.z;
-                R r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-                bool in = (r2 < lo) ? true : ((r2 > hi) ? false : exact_in_list(xr, p, q, G));
-                if (in) {
-                    if (cnt < cap) B.list[(size_t)cnt * ld + p] = (uint32_t)q | ((uint32_t)code << kCodeShift);
-                    ++cnt;
+        const R hx = g_h<R>(G, 0), hy = g_h<R>(G, 1), hz = g_h<R>(G, 2);
+        const int nx = G.ncell[0], ny = G.ncell[1], nz = G.ncell[2];
+        const int cell = B.cell[p];
+        const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
+        const R4 up = sw[p];
+        uint32_t *lp = B.list + p;
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+            int ez = cz + dz;
+            ez += (ez < 0) ? nz : ((ez >= nz) ? -nz : 0);
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                int ey = cy + dy;
+                ey += (ey < 0) ? ny : ((ey >= ny) ? -ny : 0);
+                const int row = (ez * ny + ey) * nx;
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int ex = cx + dx;
+                    ex += (ex < 0) ? nx : ((ex >= nx) ? -nx : 0);
+                    const int e = row + ex;
+                    const uint32_t code = (uint32_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)) << kCodeShift;
+                    const R ox = (R)dx * hx - up.x, oy = (R)dy * hy - up.y, oz = (R)dz * hz - up.z;
+                    const int q1 = B.cell_start[e + 1];
+                    for (int q = B.cell_start[e]; q < q1; ++q) {
+                        const R4 uq = sw[q];
+                        const R ddx = uq.x + ox, ddy = uq.y + oy, ddz = uq.z + oz;
+                        const R r2 = fma(ddz, ddz, fma(ddy, ddy, ddx * ddx));
+                        if (r2 > hi || q == p) continue;
+                        if (r2 < lo || exact_in_list(xr, p, q, G)) {
+                            if (cnt < cap) lp[(size_t)cnt * ld] = (uint32_t)q | code;
+                            ++cnt;
+                        }
+                    }
                 }
             }
         }
@@ -266,117 +276,8 @@ __global__ void k_build_list(Bufs<R> B, Geom G, int n, int ld, int cap)
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)((blockDim.x + 31) >> 5); ++w) m = max(m, smax[w]);
-        atomicMax(&st->max_nnb, m);
+        if (m > *(volatile int *)&st->max_nnb) atomicMax(&st->max_nnb, m);
     }
-}
-
-
-// Verlet list, one warp per cell.  The atoms of the 27 stencil cells (in
-// stencil order, ascending id inside a cell) are the candidates of every atom
-// of the cell: lane L takes candidates L, L+32, ... of that sequence and tests
-// each against all atoms of the cell; a ballot appends the accepted ones to
-// each atom's list in candidate order, so every list is in the same order as
-// a per-atom scan of the stencil.  Screening is in R on the cell-centred
-// coordinates; candidates within the rounding margin of r_list are decided by
-// exact_in_list.
-template <class R>
-__global__ void __launch_bounds__(256) k_build_list_cells(Bufs<R> B, Geom G, int ld, int cap)
-{
-    using R4 = typename V4<R>::T;
-    __shared__ R4 sh[27];
-    __shared__ R4 s_u[8][32];
-    __shared__ int s_cnt[8][32];
-    DevState *st = B.st;
-    if (!st->need_rebuild) return;
-    fill_shift<R>(sh, G);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (c >= G.ncells) return;
-    const int sp = st->sp, s = st->set;
-    const R4 *sw = B.shadow[sp];
-    const double *const xr[3] = {B.xr[s][0], B.xr[s][1], B.xr[s][2]};
-    const R lo = g_screen_lo<R>(G), hi = g_screen_hi<R>(G);
-    const int cx = c % G.ncell[0], cy = (c / G.ncell[0]) % G.ncell[1], cz = c / (G.ncell[0] * G.ncell[1]);
-    // lane L < 27: start and size of stencil cell L
-    int e_start = 0, e_cnt = 0;
-    if (lane < 27) {
-        int ex = cx + lane % 3 - 1, ey = cy + (lane / 3) % 3 - 1, ez = cz + lane / 9 - 1;
-        ex += (ex < 0) ? G.ncell[0] : ((ex >= G.ncell[0]) ? -G.ncell[0] : 0);
-        ey += (ey < 0) ? G.ncell[1] : ((ey >= G.ncell[1]) ? -G.ncell[1] : 0);
-        ez += (ez < 0) ? G.ncell[2] : ((ez >= G.ncell[2]) ? -G.ncell[2] : 0);
-        const int e = (ez * G.ncell[1] + ey) * G.ncell[0] + ex;
-        e_start = B.cell_start[e];
-        e_cnt = B.cell_start[e + 1] - e_start;
-    }
-    int incl = e_cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    const int excl = incl - e_cnt;
-    const int a0 = B.cell_start[c], na = B.cell_start[c + 1] - a0;
-    const unsigned lt = (1u << lane) - 1u;
-    int my_max = 0;
-    for (int base = 0; base < na; base += 32) {
-        const int nb = min(32, na - base);
-        if (lane < nb) {
-            s_u[warp][lane] = sw[a0 + base + lane];
-            s_cnt[warp][lane] = 0;
-        }
-        __syncwarp();
-        for (int m0 = 0; m0 < total; m0 += 32) {
-            const int m = m0 + lane;
-            // stencil cell of candidate m: the last code whose offset is <= m
-            int code = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int probe = min(code + step, 26);
-                const int off = __shfl_sync(0xffffffffu, excl, probe);
-                if (code + step <= 26 && off <= m) code = probe;
-            }
-            const int st0 = __shfl_sync(0xffffffffu, e_start, code);
-            const int of0 = __shfl_sync(0xffffffffu, excl, code);
-            const bool valid = m < total;
-            const int q = st0 + (m - of0);
-            R4 wq = mk4<R>(0, 0, 0, 0);
-            if (valid) {
-                const R4 uq = sw[q];
-                const R4 shf = sh[code];
-                wq = mk4<R>(uq.x + shf.x, uq.y + shf.y, uq.z + shf.z, (R)0);
-            }
-            for (int a = 0; a < nb; ++a) {
-                const int p = a0 + base + a;
-                const R4 up = s_u[warp][a];
-                bool in = false;
-                if (valid && q != p) {
-                    const R dx = wq.x - up.x, dy = wq.y - up.y, dz = wq.z - up.z;
-                    const R r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-                    in = (r2 < lo) ? true : ((r2 > hi) ? false : exact_in_list(xr, p, q, G));
-                }
-                const unsigned mask = __ballot_sync(0xffffffffu, in);
-                const int cnt0 = s_cnt[warp][a];
-                if (in) {
-                    const int pos = cnt0 + __popc(mask & lt);
-                    if (pos < cap) B.list[(size_t)pos * ld + p] = (uint32_t)q | ((uint32_t)code << kCodeShift);
-                }
-                __syncwarp();
-                if (lane == 0) s_cnt[warp][a] = cnt0 + __popc(mask);
-                __syncwarp();
-            }
-        }
-        if (lane < nb) {
-            const int cnt = s_cnt[warp][lane];
-            B.nnb[a0 + base + lane] = min(cnt, cap);
-            if (cnt > cap) atomicOr(&st->error, ERR_LIST_OVERFLOW);
-            my_max = max(my_max, cnt);
-        }
-        __syncwarp();
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) my_max = max(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
-    if (lane == 0 && my_max > *(volatile int *)&st->max_nnb) atomicMax(&st->max_nnb, my_max);
 }
 
 // --------------------------------------------------------------------------
@@ -504,7 +405,7 @@ int launch_rebuild(const Bufs<R> &B, const Geom &G, const Launch &L)
     k_cell_sort<R><<<blocks_for(G.ncells, 256), 256, 0, L.stream>>>(B, G.ncells);
     k_permute<R><<<nb, b, 0, L.stream>>>(B, G, L.n);
     k_rebuild_finish<R><<<1, 1, 0, L.stream>>>(B, L.use_cond);
-    k_build_list_cells<R><<<blocks_for(G.ncells, 8), 256, 0, L.stream>>>(B, G, L.ld, L.cap);
+    k_build_list<R><<<nb, b, 0, L.stream>>>(B, G, L.n, L.ld, L.cap);
     return 8;
 }
 

@@ -383,3 +383,70 @@ def replica_batch(nrep: int = 512, n_min: int = 1024, n_max: int = 16384, seed: 
         cells = _near_box(max(1, int(round(sizes[r] / per_cell))), min_cells)
         out.append(thermal_system(p, cells, 0.02, float(temps[r]), seed + r, label=f"rep{r}"))
     return out
+
+
+# --------------------------------------------------------------------------
+# strong-scaling sweep and the Sigma-5 tilt-boundary bicrystal
+
+SWEEP_CUBES = (8, 11, 15, 21, 28, 39, 54)  # 2 n^3 atoms: 1,024 ... 314,928
+
+
+def sweep_systems(temperature: float = 1000.0):
+    """BCC cubes of 1,024 to 314,928 atoms (geometric), then the 799,496-atom
+    box, at the given temperature."""
+    out = [bcc_cube(n, temperature=temperature, seed=SEED_BASE + 200 + n) for n in SWEEP_CUBES]
+    out.append(thermal_system(BCC_TA_LIKE, (74, 74, 73), 0.02, temperature, SEED_BASE + 274,
+                              label="bcc_799496"))
+    return out
+
+
+def sigma5_bicrystal(periods=(25, 10, 25), temperature: float = 1000.0, seed: int = SEED_BASE + 500,
+                     min_sep: float = 0.3) -> System:
+    """Sigma-5 (310)[001] symmetric tilt bicrystal of the BCC stand-in: two
+    grains rotated by -+atan(1/3) (18.43 degrees) about z, so that [310] of
+    the lower grain and [3-10] of the upper grain both lie along x.  One
+    periodic cell of a grain is a sqrt(10) x a sqrt(10) x a with 20 atoms; the
+    box holds periods[0] x (2 periods[1]) x periods[2] of them, the grains
+    stacked along y (boundaries at y = 0 and y = L_y / 2).  Upper-grain atoms
+    closer than min_sep * a to a lower-grain atom are removed.  Thermal
+    displacements and Maxwell velocities at `temperature`."""
+    p = BCC_TA_LIKE
+    a = p.a
+    s10 = math.sqrt(10.0)
+    Lx, Ly, Lz = periods[0] * a * s10, 2 * periods[1] * a * s10, periods[2] * a
+    box = np.array([Lx, Ly, Lz])
+    basis = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.5]])
+    grains = []
+    for g, sign in enumerate((1.0, -1.0)):
+        # columns: where lattice vectors x, y go; (3, sign, 0) a maps to +x
+        c, s = 3.0 / s10, sign * 1.0 / s10
+        R = np.array([[c, s], [-s, c]])
+        y0, y1 = (0.0, Ly / 2) if g == 0 else (Ly / 2, Ly)
+        span = int(math.ceil(max(Lx, Ly) / a)) + 4
+        ii, jj = np.meshgrid(np.arange(-span, 2 * span), np.arange(-span, 2 * span), indexing="ij")
+        pts = []
+        for bvec in basis:
+            xy = (np.stack([ii.ravel() + bvec[0], jj.ravel() + bvec[1]], 1) * a) @ R.T
+            eps = 1e-7
+            keep = (xy[:, 0] >= -eps) & (xy[:, 0] < Lx - eps) & (xy[:, 1] >= y0 - eps) & (xy[:, 1] < y1 - eps)
+            xy = xy[keep]
+            for k in range(periods[2]):
+                z = np.full((xy.shape[0], 1), (k + bvec[2]) * a)
+                pts.append(np.hstack([xy, z]))
+        grains.append(np.vstack(pts))
+    lower, upper = grains
+
+    def inbox(x):
+        w = np.mod(x, box)
+        return np.where(w >= box, w - box, w)
+
+    from scipy.spatial import cKDTree  # input construction only
+    tree = cKDTree(inbox(lower), boxsize=box)
+    dist, _ = tree.query(inbox(upper), k=1)
+    upper = upper[dist >= min_sep * a]
+    pos = inbox(np.vstack([lower, upper]))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pos = displace(pos, box, 0.02, rng)
+    vel = maxwell(pos.shape[0], p.mass, temperature, rng)
+    return System(box=box, pos=pos, vel=vel, types=np.zeros(pos.shape[0], np.int32),
+                  pot=johnson_potential(p), label="sigma5_bicrystal")
