@@ -233,7 +233,9 @@ def run_ours(args):
             "clocks": clk,
             "stats": {"rebuilds": st["rebuilds"], "max_neighbors": st["max_neighbors"],
                       "lanes_density": st["lanes_density"], "lanes_force": st["lanes_force"],
-                      "rows_density": st["rows_density"], "rows_force": st["rows_force"]},
+                      "rows_density": st["rows_density"], "rows_force": st["rows_force"],
+                      "tiles_density": st["tiles_density"], "tiles_force": st["tiles_force"],
+                      "table_density": st["table_density"], "table_force": st["table_force"]},
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu

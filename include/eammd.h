@@ -82,7 +82,8 @@ typedef struct {
 } md_potential;
 
 enum { MD_PRECISION_FP64 = 0, MD_PRECISION_MIXED = 1 };
-enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2 };
+enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2, MD_SCHEDULE_TILES = 3,
+       MD_SCHEDULE_TABLE = 4 };
 
 /* Options.  Fill with md_options_default() and change what you need.
  *   precision        MD_PRECISION_FP64: all arithmetic in FP64.
@@ -105,7 +106,8 @@ enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2 };
  *   block_size       threads per block of the per-atom kernels (0 = 256).
  *   lanes_per_atom   threads that share one atom's neighbour list in the
  *                    density and force passes: 1, 2, 4 or 8; 0 = chosen at
- *                    md_create by timing each (the choice is kept for the
+ *                    md_create by timing each (with the schedule and, for
+ *                    the atom-parallel passes, threads per block) (the choice is kept for the
  *                    process, per precision and size class, so contexts of
  *                    the same shape follow the same schedule).  Results
  *                    depend on it only through FP summation order.
@@ -123,6 +125,18 @@ enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2 };
  *                    md_create, the atom-parallel gathers are used.  Forces
  *                    are bitwise those of MD_SCHEDULE_ATOMS with the same
  *                    lanes_per_atom; energy sums differ in rounding only.
+ *                    MD_SCHEDULE_TILES: atom-parallel (lanes_per_atom 1, 2
+ *                    or 4, one atom type with a shared knot grid), each
+ *                    block first bulk-copies its atoms' list columns into
+ *                    shared memory; results bitwise those of
+ *                    MD_SCHEDULE_ATOMS.  A bulk copy that has not landed
+ *                    within 1 s raises MD_ERR_TIMEOUT at the next md_sync.
+ *                    MD_SCHEDULE_TABLE: mixed precision, one atom type with a
+ *                    shared knot grid: persistent blocks (as many as fit on
+ *                    the GPU at once) each copy the spline rows into shared
+ *                    memory and walk tiles of atoms; lanes_per_atom 1, 2 or
+ *                    4; forces bitwise those of MD_SCHEDULE_ATOMS.  Falls
+ *                    back to MD_SCHEDULE_ATOMS where it does not apply.
  *   stage_capacity   records a row-staged block holds; 0 = 1.1 x the most
  *                    that any 3 x 3 block of rows holds at md_create, + 32.
  *                    Must fit the shared memory of a block (160 KB of
@@ -207,7 +221,12 @@ typedef struct {
     int32_t rows_density;    /* 1: density pass row-staged (MD_SCHEDULE_ROWS) */
     int32_t rows_force;      /* 1: force pass row-staged */
     int32_t stage_capacity;  /* records a row-staged block holds (0: none) */
-    int32_t reserved;
+    int32_t tiles_density;   /* 1: density pass list-tiled (MD_SCHEDULE_TILES) */
+    int32_t tiles_force;     /* 1: force pass list-tiled */
+    int32_t table_density;   /* 1: density pass with shared-memory spline rows */
+    int32_t table_force;     /* 1: force pass likewise */
+    int32_t threads_density; /* threads per block of the density pass */
+    int32_t threads_force;   /* threads per block of the force pass */
 } md_stats_t;
 
 md_status md_stats(md_ctx *ctx, md_stats_t *out);

@@ -24,7 +24,7 @@ STATUS = {0: "MD_OK", -1: "MD_ERR_ARG", -2: "MD_ERR_BOX", -3: "MD_ERR_CUDA", -4:
           -5: "MD_ERR_NONFINITE", -6: "MD_ERR_TIMEOUT", -7: "MD_ERR_LIST_OVERFLOW",
           -8: "MD_ERR_CAPACITY"}
 PRECISION = {"fp64": 0, "mixed": 1}
-SCHEDULE = {"auto": 0, "atoms": 1, "rows": 2}
+SCHEDULE = {"auto": 0, "atoms": 1, "rows": 2, "tiles": 3, "table": 4}
 
 # every entry point declared in include/eammd.h
 EXPORTS = ("md_options_default", "md_create", "md_step", "md_sync", "md_energy", "md_forces",
@@ -63,7 +63,10 @@ class Stats(C.Structure):
                 ("list_capacity", C.c_int32), ("table_out_of_range", C.c_int64),
                 ("kernel_launches", C.c_int64), ("lanes_density", C.c_int32),
                 ("lanes_force", C.c_int32), ("rows_density", C.c_int32),
-                ("rows_force", C.c_int32), ("stage_capacity", C.c_int32), ("reserved", C.c_int32)]
+                ("rows_force", C.c_int32), ("stage_capacity", C.c_int32), ("tiles_density", C.c_int32),
+                ("tiles_force", C.c_int32), ("table_density", C.c_int32),
+                ("table_force", C.c_int32), ("threads_density", C.c_int32),
+                ("threads_force", C.c_int32)]
 
 
 class Profile(C.Structure):

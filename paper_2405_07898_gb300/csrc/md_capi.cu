@@ -572,15 +572,42 @@ md_status build_tables(md_ctx *ctx, const md_potential *pot, std::vector<double>
     return MD_OK;
 }
 
-void set_lanes(md_ctx *ctx, int tpa_d, int tpa_f, int rows_d, int rows_f)
+// Schedule of one pass: lanes per atom and where its gathers read from.
+enum SchedKind { SCHED_ATOMS = 0, SCHED_ROWS = 1, SCHED_TILES = 2, SCHED_TABLE = 3 };
+struct PassSched {
+    int tpa, kind, block;  // block 0: the context's block_size
+};
+
+void set_sched(md_ctx *ctx, PassSched d, PassSched f)
 {
     Launch &L = ctx->L;
-    L.tpa_d = tpa_d;
-    L.tpa_f = tpa_f;
-    L.staged_d = rows_d;
-    L.staged_f = rows_f;
-    L.nb_d = rows_d ? L.nrows : blocks_for_host((int64_t)L.n * tpa_d, L.block);
-    L.nb_f = rows_f ? L.nrows : blocks_for_host((int64_t)L.n * tpa_f, L.block);
+    L.tpa_d = d.tpa;
+    L.tpa_f = f.tpa;
+    L.staged_d = d.kind == SCHED_ROWS;
+    L.staged_f = f.kind == SCHED_ROWS;
+    L.tiled_d = d.kind == SCHED_TILES;
+    L.tiled_f = f.kind == SCHED_TILES;
+    L.tab_d = d.kind == SCHED_TABLE;
+    L.tab_f = f.kind == SCHED_TABLE;
+    L.block_d = d.block > 0 ? d.block : L.block;
+    L.block_f = f.block > 0 ? f.block : L.block;
+    L.nb_d = L.staged_d ? L.nrows
+                        : (L.tab_d ? table_grid(L, false, d.tpa, L.block_d)
+                                   : blocks_for_host((int64_t)L.n * d.tpa, L.block_d));
+    L.nb_f = L.staged_f ? L.nrows
+                        : (L.tab_f ? table_grid(L, true, f.tpa, L.block_f)
+                                   : blocks_for_host((int64_t)L.n * f.tpa, L.block_f));
+}
+
+// Whether the shared-table passes can run: FP32 pair arithmetic, fused
+// tables, rows that fit the shared memory of a block, and at least one
+// resident block.
+bool table_usable(md_ctx *ctx, int tpa)
+{
+    const Launch &L = ctx->L;
+    return ctx->precision == MD_PRECISION_MIXED && !L.multi && L.nint_fused > 0 &&
+           table_smem_bytes(L, true) <= (size_t)kSharedLimitBytes && table_grid(L, true, tpa, L.block) > 0 &&
+           table_grid(L, false, tpa, L.block) > 0;
 }
 
 // Choices of the autotuner, per (precision, type path, size bucket), kept for
@@ -590,14 +617,10 @@ struct TuneKey {
     int precision, multi, bucket;
 };
 struct TuneChoice {
-    int tpa_d, tpa_f, rows_d, rows_f;
+    PassSched d, f;
 };
 std::mutex g_tune_mu;
 std::vector<std::pair<TuneKey, TuneChoice>> g_tune_cache;
-
-// Largest dynamic shared memory of a row-staged block.  The attribute only
-// permits it; occupancy follows what a launch asks for.
-constexpr int kStageLimitBytes = 160 * 1024;
 
 // Stage capacity of the row-staged passes from the cell occupancy of the
 // current list build: the most records any 3 x 3 block of rows holds, with
@@ -609,8 +632,12 @@ md_status setup_staging(md_ctx *ctx)
     Launch &L = ctx->L;
     L.stage_cap = 0;
     const md_options &o = ctx->opt;
+    if (L.multi || ctx->n == 0) return MD_OK;
+    // the attribute only permits the shared memory; occupancy follows what a
+    // launch asks for
+    CK(allow_shared_staging<R>(kSharedLimitBytes));
     const bool wanted = o.schedule == MD_SCHEDULE_ROWS || (o.schedule == MD_SCHEDULE_AUTO && o.lanes_per_atom == 0);
-    if (L.multi || !wanted || ctx->n == 0) return MD_OK;
+    if (!wanted) return MD_OK;
     const Geom &G = ctx->G;
     const int nx = G.ncell[0], ny = G.ncell[1], nz = G.ncell[2];
     std::vector<int> cs((size_t)G.ncells + 1);
@@ -631,11 +658,10 @@ md_status setup_staging(md_ctx *ctx)
         }
     const int64_t cap = o.stage_capacity > 0 ? (int64_t)o.stage_capacity
                                              : ((int64_t)std::ceil(1.1 * (double)most) + 32 + 31) / 32 * 32;
-    if (cap * (int64_t)sizeof(typename V4<R>::T) > kStageLimitBytes) {
+    if (cap * (int64_t)sizeof(typename V4<R>::T) > kSharedLimitBytes) {
         if (o.stage_capacity > 0) return ctx->fail(MD_ERR_ARG, "stage_capacity exceeds the shared memory of a block");
         return MD_OK;
     }
-    CK(allow_row_staging<R>(kStageLimitBytes));
     L.stage_cap = (int)cap;
     return MD_OK;
 }
@@ -654,33 +680,48 @@ md_status reevaluate(md_ctx *ctx)
     return MD_OK;
 }
 
-// Schedule of the density and force passes: time the atom-parallel passes
-// with 1, 2, 4, 8 lanes per atom and, where a stage was sized, the
-// row-staged passes with 1, 2, 4, on the current state (density, and forces
-// without integration; neither changes positions or velocities) and keep the
-// fastest of each.
+// Schedule of the density and force passes: time, on the current state
+// (density, and forces without integration; neither changes positions or
+// velocities), the atom-parallel passes with 1, 2, 4, 8 lanes per atom
+// gathering the list from device memory, and, on the one-type path, with 1,
+// 2, 4 lanes from a shared-memory list tile and row-staged with 1, 2, 4
+// (where a stage was sized); keep the fastest of each pass.
 template <class R>
 md_status autotune(md_ctx *ctx)
 {
     int bucket = 0;
     for (int64_t m = ctx->n; m > 1; m >>= 1) ++bucket;
     TuneKey key{ctx->precision, ctx->L.multi, bucket};
+    auto usable = [&](const PassSched &p) {
+        return (p.kind != SCHED_ROWS || ctx->L.stage_cap > 0) && (p.kind != SCHED_TABLE || table_usable(ctx, p.tpa));
+    };
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         for (auto &e : g_tune_cache)
             if (e.first.precision == key.precision && e.first.multi == key.multi && e.first.bucket == key.bucket) {
-                const TuneChoice &c = e.second;
-                const bool ok = ctx->L.stage_cap > 0 || (!c.rows_d && !c.rows_f);
-                set_lanes(ctx, c.tpa_d, c.tpa_f, ok && c.rows_d, ok && c.rows_f);
+                PassSched d = e.second.d, f = e.second.f;
+                if (!usable(d)) d = {d.tpa, SCHED_ATOMS, d.block};
+                if (!usable(f)) f = {f.tpa, SCHED_ATOMS, f.block};
+                set_sched(ctx, d, f);
                 return reevaluate<R>(ctx);
             }
     }
     const Bufs<R> &B = bufs<R>(ctx);
-    struct Cand {
-        int tpa, rows;
-    };
-    std::vector<Cand> cand = {{1, 0}, {2, 0}, {4, 0}, {8, 0}};
-    if (ctx->L.stage_cap > 0) cand.insert(cand.end(), {{1, 1}, {2, 1}, {4, 1}});
+    // block sizes below 256 let the atom-parallel passes fill their last
+    // wave of blocks on the GPU
+    std::vector<PassSched> cand;
+    for (int t : {1, 2})
+        for (int b : {256, 224, 192, 160, 128}) cand.push_back({t, SCHED_ATOMS, b});
+    cand.push_back({4, SCHED_ATOMS, 256});
+    cand.push_back({8, SCHED_ATOMS, 256});
+    if (!ctx->L.multi) {
+        for (int t : {1, 2, 4})
+            if (list_tile_bytes(ctx->L, t, 256) <= (size_t)kSharedLimitBytes) cand.push_back({t, SCHED_TILES, 256});
+        if (ctx->L.stage_cap > 0)
+            for (int t : {1, 2, 4}) cand.push_back({t, SCHED_ROWS, 256});
+        for (int t : {1, 2, 4})
+            if (table_usable(ctx, t)) cand.push_back({t, SCHED_TABLE, 256});
+    }
     const int nc = (int)cand.size();
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -691,7 +732,7 @@ md_status autotune(md_ctx *ctx)
     const int rounds = 6;
     for (int round = 0; round < rounds; ++round) {
         for (int ci = 0; ci < nc; ++ci) {
-            set_lanes(ctx, cand[ci].tpa, cand[ci].tpa, cand[ci].rows, cand[ci].rows);
+            set_sched(ctx, cand[ci], cand[ci]);
             Launch L = ctx->L;
             L.use_cond = 0;
             float ms = 0;
@@ -720,12 +761,12 @@ md_status autotune(md_ctx *ctx)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    const TuneChoice choice{cand[cd].tpa, cand[cf].tpa, cand[cd].rows, cand[cf].rows};
+    const TuneChoice choice{cand[cd], cand[cf]};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune_cache.push_back({key, choice});
     }
-    set_lanes(ctx, choice.tpa_d, choice.tpa_f, choice.rows_d, choice.rows_f);
+    set_sched(ctx, choice.d, choice.f);
     // forces and energies of the state under the chosen schedule
     md_status rc = reevaluate<R>(ctx);
     if (rc != MD_OK) return rc;
@@ -878,6 +919,7 @@ md_status create_impl(md_ctx *ctx, const double *pos, const double *vel, const i
     md_status trc = build_tables<R>(ctx, pot, rows, rows2, tab);
     if (trc != MD_OK) return trc;
     ctx->L.multi = tab.fused ? 0 : 1;
+    ctx->L.nint_fused = tab.fused ? tab.fphi.nint : 0;
     ctx->shapes.clear();
     for (int t = 0; t < pot->ntypes; ++t) ctx->shapes.push_back(pot->F[t]);
     for (int t = 0; t < pot->ntypes; ++t) ctx->shapes.push_back(pot->f[t]);
@@ -903,9 +945,17 @@ md_status create_impl(md_ctx *ctx, const double *pos, const double *vel, const i
     rc = setup_staging<R>(ctx);
     if (rc != MD_OK) return rc;
     const md_options &o = ctx->opt;
-    if (o.schedule == MD_SCHEDULE_ROWS && !ctx->L.multi) {
-        const int lanes = o.lanes_per_atom > 0 ? o.lanes_per_atom : 2;
-        set_lanes(ctx, lanes, lanes, 1, 1);
+    const int forced_lanes = o.lanes_per_atom > 0 ? o.lanes_per_atom : 2;
+    const bool forced = (o.schedule == MD_SCHEDULE_ROWS || o.schedule == MD_SCHEDULE_TILES) ||
+                        (o.schedule == MD_SCHEDULE_TABLE && table_usable(ctx, forced_lanes));
+    if (forced && !ctx->L.multi) {
+        const int lanes = forced_lanes;
+        const PassSched p{lanes,
+                          o.schedule == MD_SCHEDULE_ROWS    ? SCHED_ROWS
+                          : o.schedule == MD_SCHEDULE_TILES ? SCHED_TILES
+                                                            : SCHED_TABLE,
+                          0};
+        set_sched(ctx, p, p);
         rc = reevaluate<R>(ctx);
         if (rc != MD_OK) return rc;
         return check_device_errors(ctx);
@@ -984,10 +1034,10 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     if (!(o.lanes_per_atom == 0 || o.lanes_per_atom == 1 || o.lanes_per_atom == 2 || o.lanes_per_atom == 4 ||
           o.lanes_per_atom == 8))
         return bad(MD_ERR_ARG, "lanes_per_atom must be 0 (tune), 1, 2, 4 or 8");
-    if (o.schedule < MD_SCHEDULE_AUTO || o.schedule > MD_SCHEDULE_ROWS)
-        return bad(MD_ERR_ARG, "schedule must be MD_SCHEDULE_AUTO, _ATOMS or _ROWS");
-    if (o.schedule == MD_SCHEDULE_ROWS && o.lanes_per_atom == 8)
-        return bad(MD_ERR_ARG, "row-staged passes take 1, 2 or 4 lanes per atom");
+    if (o.schedule < MD_SCHEDULE_AUTO || o.schedule > MD_SCHEDULE_TABLE)
+        return bad(MD_ERR_ARG, "schedule must be MD_SCHEDULE_AUTO, _ATOMS, _ROWS, _TILES or _TABLE");
+    if (o.schedule >= MD_SCHEDULE_ROWS && o.lanes_per_atom == 8)
+        return bad(MD_ERR_ARG, "row-staged, list-tiled and shared-table passes take 1, 2 or 4 lanes per atom");
     if (o.stage_capacity < 0) return bad(MD_ERR_ARG, "stage_capacity must be >= 0");
 
     md_ctx *ctx = new (std::nothrow) md_ctx();
@@ -1042,10 +1092,11 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     L.block = o.block_size;
     L.nblocks = (int)((n + L.block - 1) / L.block);
     L.nrows = G.ncell[1] * G.ncell[2];
-    L.pstride = std::max({1, blocks_for_host(8 * n, L.block), L.nrows});
+    L.pstride = std::max({1, blocks_for_host(8 * n, std::min(L.block, 128)), L.nrows});
     {
         int lanes = o.lanes_per_atom > 0 ? o.lanes_per_atom : 4;
         L.tpa_d = L.tpa_f = lanes;
+        L.block_d = L.block_f = L.block;
         L.nb_d = L.nb_f = blocks_for_host(n * lanes, L.block);
     }
     L.ntypes = pot->ntypes;
@@ -1228,8 +1279,13 @@ md_status md_stats(md_ctx *ctx, md_stats_t *out)
     out->lanes_force = ctx->L.tpa_f;
     out->rows_density = ctx->L.staged_d;
     out->rows_force = ctx->L.staged_f;
+    out->tiles_density = ctx->L.tiled_d;
+    out->tiles_force = ctx->L.tiled_f;
+    out->table_density = ctx->L.tab_d;
+    out->table_force = ctx->L.tab_f;
+    out->threads_density = ctx->L.block_d;
+    out->threads_force = ctx->L.block_f;
     out->stage_capacity = ctx->L.stage_cap;
-    out->reserved = 0;
     return MD_OK;
 }
 

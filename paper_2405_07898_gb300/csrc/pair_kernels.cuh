@@ -85,41 +85,137 @@ struct StagedFetch {
     }
 };
 
+// Where the spline rows of the one-type path are read from: coef2 in device
+// memory (row 2k: f, row 2k+1: phi, both in one 32-byte load) or a copy in
+// shared memory with the f and phi rows in two arrays, so that 16-byte reads
+// at scattered rows spread over all banks.
+template <class R>
+struct TabGlobal {
+    const typename V4<R>::T *coef2;
+    __device__ __forceinline__ typename V4<R>::T f(int kk) const { return coef2[2 * kk]; }
+    __device__ __forceinline__ void fphi(int kk, typename V4<R>::T &cf, typename V4<R>::T &cp) const
+    {
+        load_row2<R>(coef2 + 2 * kk, cf, cp);
+    }
+};
+struct TabShared {
+    const float4 *f_rows, *phi_rows;
+    __device__ __forceinline__ float4 f(int kk) const { return f_rows[kk]; }
+    __device__ __forceinline__ void fphi(int kk, float4 &cf, float4 &cp) const
+    {
+        cf = f_rows[kk];
+        cp = phi_rows[kk];
+    }
+};
+
+// Where list column k of the lane's atom is read from.
+struct ListGlobal {
+    const uint32_t *lp;  // list + i
+    int ld;
+    __device__ __forceinline__ uint32_t operator()(int k) const { return lp[(size_t)k * ld]; }
+};
+struct ListTile {
+    const uint32_t *tp;  // tile + (i - i0)
+    int width;           // atoms per tile column
+    __device__ __forceinline__ uint32_t operator()(int k) const { return tp[k * width]; }
+};
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of an mbarrier for at most limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns)
+{
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
+
+// Columns 0 .. ncol-1 of the list of atoms [i0, i0 + width) into the block's
+// tile (column k at tile + k * width) by bulk asynchronous copies, one per
+// column, that complete on one mbarrier.  Every column is a contiguous,
+// 128-byte aligned run of the list (ld and width are multiples of 32 atoms).
+// Returns false (and flags ERR_TIMEOUT) if the copies did not land within
+// the wait limit; the caller then reads the list from device memory.
+__device__ __forceinline__ bool stage_list(const uint32_t *list, int ld, int i0, int width, int ncol,
+                                           uint32_t *tile, unsigned int *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t bar_a = (uint32_t)__cvta_generic_to_shared(&bar);
+    const int w = min(width, ld - i0);
+    const uint32_t col_bytes = (uint32_t)w * 4u;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(col_bytes * (uint32_t)ncol)
+                     : "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        for (int k = threadIdx.x; k < ncol; k += 32) {
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(tile + (size_t)k * width);
+            const uint32_t *src = list + (size_t)k * ld + i0;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                "l"(src), "r"(col_bytes), "r"(bar_a)
+                : "memory");
+        }
+    }
+    if (mbar_wait(bar_a, 0, kWaitLimitNs)) return true;
+    atomicOr(err, ERR_TIMEOUT);
+    mbar_wait(bar_a, 0, kWaitLimitNs);  // the copies still own the tile
+    return false;
+}
+
 // This lane's part of rho_i = sum over listed j with r < r_cut of f_{t_j}(r_ij)
 // (Eq. 2).
-template <class R, bool MULTI, int TPA, class Fetch>
-__device__ __forceinline__ R density_lane(const Bufs<R> &B, const Launch &L, const typename V4<R>::T *sh, R rc2,
-                                          int s, int i, int l, const typename V4<R>::T &ui, const Fetch &fetch)
+template <class R, bool MULTI, int TPA, int U, class List, class Fetch, class Tab>
+__device__ __forceinline__ R density_lane(const Bufs<R> &B, const typename V4<R>::T *sh, R rc2, int s, int nn,
+                                          int l, const typename V4<R>::T &ui, const List &list, const Fetch &fetch,
+                                          const Tab &tab)
 {
     using R4 = typename V4<R>::T;
     const Tables<R> &T = *B.tables;
     const SplineDesc<R> g = MULTI ? T.f[0] : T.fphi;
-    const int nn = B.nnb[i];
-    const uint32_t *lp = B.list + i;
     R rho = (R)0;
-    for (int k = l; k < nn; k += 2 * TPA) {
-        const bool two = k + TPA < nn;
-        const uint32_t e0 = lp[(size_t)k * L.ld];
-        const uint32_t e1 = two ? lp[(size_t)(k + TPA) * L.ld] : e0;
-        const R4 u0 = fetch(e0);
-        const R4 u1 = fetch(e1);
-        const PairIn<R> p0 = pair_vector<R>(ui, u0, sh[e0 >> kCodeShift]);
-        const PairIn<R> p1 = pair_vector<R>(ui, u1, sh[e1 >> kCodeShift]);
+    // U pairs per round (columns k, k + TPA, ...), all gathers issued before
+    // any is used; the sum runs in column order
+    for (int k = l; k < nn; k += U * TPA) {
+        uint32_t e[U];
+        R4 u[U];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const PairIn<R> &p = q ? p1 : p0;
-            if ((q == 0 || two) && p.r2 < rc2) {
+        for (int q = 0; q < U; ++q) e[q] = (k + q * TPA < nn) ? list(k + q * TPA) : 0u;
+#pragma unroll
+        for (int q = 0; q < U; ++q) u[q] = fetch(q == 0 || k + q * TPA < nn ? e[q] : e[0]);
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const PairIn<R> p = pair_vector<R>(ui, u[q], sh[e[q] >> kCodeShift]);
+            if ((q == 0 || k + q * TPA < nn) && p.r2 < rc2) {
                 R rinv, r;
                 inv_r(p.r2, rinv, r);
                 if (MULTI) {
                     R val, der;
-                    const int j = (int)((q ? e1 : e0) & kIndexMask);
+                    const int j = (int)(e[q] & kIndexMask);
                     spline_r(T.f[B.type[s][j]], B.coef, r, val, der);
                     rho += val;
                 } else {
                     R t;
                     const int kk = segment(g, r, t);
-                    const R4 c = B.coef2[2 * kk];
+                    const R4 c = tab.f(kk);
                     rho += fma(t, fma(t, fma(t, c.w, c.z), c.y), c.x);
                 }
             }
@@ -145,35 +241,33 @@ __device__ __forceinline__ R embed(const Bufs<R> &B, typename V4<R>::T *sw, int 
 //   F_i  = sum_j s_ij (x_j - x_i) / r,
 // and, when ENERGY, of the pair energy and the virial (e7: pair energy, then
 // W xx yy zz xy xz yz).
-template <class R, bool MULTI, bool ENERGY, int TPA, class Fetch>
+template <class R, bool MULTI, bool ENERGY, int TPA, int U, class List, class Fetch, class Tab>
 __device__ __forceinline__ void force_lane(const Bufs<R> &B, const Launch &L, const typename V4<R>::T *sh, R rc2,
-                                           int s, int i, int l, int ti, const typename V4<R>::T &ui,
-                                           const Fetch &fetch, R (&f)[3], R (&e7)[7])
+                                           int s, int nn, int l, int ti, const typename V4<R>::T &ui,
+                                           const List &list, const Fetch &fetch, R (&f)[3], R (&e7)[7],
+                                           const Tab &tab)
 {
     using R4 = typename V4<R>::T;
     const Tables<R> &T = *B.tables;
     const SplineDesc<R> g = T.fphi;
     const R Fpi = ui.w;
-    const int nn = B.nnb[i];
-    const uint32_t *lp = B.list + i;
-    for (int k = l; k < nn; k += 2 * TPA) {
-        const bool two = k + TPA < nn;
-        const uint32_t e0 = lp[(size_t)k * L.ld];
-        const uint32_t e1 = two ? lp[(size_t)(k + TPA) * L.ld] : e0;
-        const R4 u0 = fetch(e0);
-        const R4 u1 = fetch(e1);
-        const PairIn<R> p0 = pair_vector<R>(ui, u0, sh[e0 >> kCodeShift]);
-        const PairIn<R> p1 = pair_vector<R>(ui, u1, sh[e1 >> kCodeShift]);
+    for (int k = l; k < nn; k += U * TPA) {
+        uint32_t e[U];
+        R4 u[U];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const PairIn<R> &p = q ? p1 : p0;
-            if ((q == 0 || two) && p.r2 < rc2) {
+        for (int q = 0; q < U; ++q) e[q] = (k + q * TPA < nn) ? list(k + q * TPA) : 0u;
+#pragma unroll
+        for (int q = 0; q < U; ++q) u[q] = fetch(q == 0 || k + q * TPA < nn ? e[q] : e[0]);
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const PairIn<R> p = pair_vector<R>(ui, u[q], sh[e[q] >> kCodeShift]);
+            if ((q == 0 || k + q * TPA < nn) && p.r2 < rc2) {
                 R rinv, r;
                 inv_r(p.r2, rinv, r);
-                const R Fpj = q ? u1.w : u0.w;
+                const R Fpj = u[q].w;
                 R phv, phd, fdj, fdi;
                 if (MULTI) {
-                    const int j = (int)((q ? e1 : e0) & kIndexMask);
+                    const int j = (int)(e[q] & kIndexMask);
                     const int tj = B.type[s][j];
                     spline_r(T.phi[pair_index(L.ntypes, ti, tj)], B.coef, r, phv, phd);
                     fdj = spline_r_der(T.f[tj], B.coef, r);
@@ -182,7 +276,7 @@ __device__ __forceinline__ void force_lane(const Bufs<R> &B, const Launch &L, co
                     R t;
                     const int kk = segment(g, r, t);
                     R4 cf, cp;
-                    load_row2<R>(B.coef2 + 2 * kk, cf, cp);
+                    tab.fphi(kk, cf, cp);
                     fdj = fma(t, fma(t, (R)3 * cf.w, (R)2 * cf.z), cf.y);
                     fdi = fdj;
                     phd = fma(t, fma(t, (R)3 * cp.w, (R)2 * cp.z), cp.y);
@@ -261,20 +355,44 @@ __device__ __forceinline__ void force_block_end(const Bufs<R> &B, const Launch &
 
 // ---- atom-parallel schedule ----
 
-template <class R, bool MULTI, bool ENERGY, int TPA>
+// Pairs in flight per lane: the type-dependent path needs more registers a pair.
+template <bool MULTI> struct PairsInFlight {
+    static constexpr int U = MULTI ? 2 : 4;
+};
+
+extern __shared__ __align__(32) unsigned char dyn[];
+
+// LS: the block's list tile is brought into shared memory by bulk copies
+// first (one-type path only), so that the lanes' gathers do not wait on the
+// list stream.
+template <class R, bool MULTI, bool ENERGY, int TPA, bool LS>
 __global__ void __launch_bounds__(256) k_density(Bufs<R> B, Geom G, Launch L)
 {
     using R4 = typename V4<R>::T;
+    constexpr int U = PairsInFlight<MULTI>::U;
     __shared__ R4 sh[27];
     fill_shift<R>(sh, G);
     const DevState *st = B.st;
     const int sp = st->sp, s = st->set;
     R4 *sw = B.shadow[sp];
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = gt / TPA, l = gt % TPA;
+    const int width = blockDim.x / TPA;
+    const int i0 = blockIdx.x * width;
+    uint32_t *tile = reinterpret_cast<uint32_t *>(dyn);
+    const bool tiled = LS && stage_list(B.list, L.ld, i0, width, min(st->max_nnb, L.cap), tile, &B.st->error);
+    const int i = i0 + threadIdx.x / TPA, l = threadIdx.x % TPA;
     const bool active = i < L.n;
     const int ti = (MULTI && active) ? B.type[s][i] : 0;
-    R rho = active ? density_lane<R, MULTI, TPA>(B, L, sh, g_rc2<R>(G), s, i, l, sw[i], GlobalFetch<R>{sw}) : (R)0;
+    const R rc2 = g_rc2<R>(G);
+    R rho = (R)0;
+    if (active) {
+        const int nn = B.nnb[i];
+        if (tiled)
+            rho = density_lane<R, MULTI, TPA, U>(B, sh, rc2, s, nn, l, sw[i], ListTile{tile + (i - i0), width},
+                                                 GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2});
+        else
+            rho = density_lane<R, MULTI, TPA, U>(B, sh, rc2, s, nn, l, sw[i], ListGlobal{B.list + i, L.ld},
+                                                 GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2});
+    }
     rho = lane_sum<TPA>(rho);
     R e_embed = (R)0;
     if (active && l == 0) e_embed = embed<R>(B, sw, i, ti, rho);
@@ -284,23 +402,35 @@ __global__ void __launch_bounds__(256) k_density(Bufs<R> B, Geom G, Launch L)
     }
 }
 
-template <class R, bool MULTI, int MODE, bool ENERGY, int TPA>
+template <class R, bool MULTI, int MODE, bool ENERGY, int TPA, bool LS>
 __global__ void __launch_bounds__(256) k_force(Bufs<R> B, Geom G, Launch L)
 {
     using R4 = typename V4<R>::T;
+    constexpr int U = PairsInFlight<MULTI>::U;
     __shared__ R4 sh[27];
     fill_shift<R>(sh, G);
     const DevState *st = B.st;
     const int sp = st->sp, s = st->set;
     const R4 *sw = B.shadow[sp];
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = gt / TPA, l = gt % TPA;
+    const int width = blockDim.x / TPA;
+    const int i0 = blockIdx.x * width;
+    uint32_t *tile = reinterpret_cast<uint32_t *>(dyn);
+    const bool tiled = LS && stage_list(B.list, L.ld, i0, width, min(st->max_nnb, L.cap), tile, &B.st->error);
+    const int i = i0 + threadIdx.x / TPA, l = threadIdx.x % TPA;
     const bool active = i < L.n;
     const int ti = (MULTI && active) ? B.type[s][i] : 0;
+    const R rc2 = g_rc2<R>(G);
     R f[3] = {0, 0, 0};
     R e7[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (active)
-        force_lane<R, MULTI, ENERGY, TPA>(B, L, sh, g_rc2<R>(G), s, i, l, ti, sw[i], GlobalFetch<R>{sw}, f, e7);
+    if (active) {
+        const int nn = B.nnb[i];
+        if (tiled)
+            force_lane<R, MULTI, ENERGY, TPA, U>(B, L, sh, rc2, s, nn, l, ti, sw[i], ListTile{tile + (i - i0), width},
+                                                 GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2});
+        else
+            force_lane<R, MULTI, ENERGY, TPA, U>(B, L, sh, rc2, s, nn, l, ti, sw[i], ListGlobal{B.list + i, L.ld},
+                                                 GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2});
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);
     double ke = 0.0;
@@ -352,7 +482,6 @@ template <class R, bool ENERGY, int TPA>
 __global__ void __launch_bounds__(256) k_density_rows(Bufs<R> B, Geom G, Launch L)
 {
     using R4 = typename V4<R>::T;
-    extern __shared__ __align__(32) unsigned char dyn[];
     R4 *stage = reinterpret_cast<R4 *>(dyn);
     __shared__ R4 sh[27];
     __shared__ int base[9], rstart[9], rcount[9];
@@ -371,12 +500,14 @@ __global__ void __launch_bounds__(256) k_density_rows(Bufs<R> B, Geom G, Launch 
         const bool active = i < a1;
         R rho = (R)0;
         if (active) {
-            if (staged) {
-                const R4 ui = stage[i - base[4]];
-                rho = density_lane<R, false, TPA>(B, L, sh, rc2, s, i, l, ui, StagedFetch<R>{stage, base});
-            } else {
-                rho = density_lane<R, false, TPA>(B, L, sh, rc2, s, i, l, sw[i], GlobalFetch<R>{sw});
-            }
+            const int nn = B.nnb[i];
+            const ListGlobal list{B.list + i, L.ld};
+            if (staged)
+                rho = density_lane<R, false, TPA, 4>(B, sh, rc2, s, nn, l, stage[i - base[4]], list,
+                                                     StagedFetch<R>{stage, base}, TabGlobal<R>{B.coef2});
+            else
+                rho = density_lane<R, false, TPA, 4>(B, sh, rc2, s, nn, l, sw[i], list, GlobalFetch<R>{sw},
+                                                     TabGlobal<R>{B.coef2});
         }
         rho = lane_sum<TPA>(rho);
         if (active && l == 0) e_embed += embed<R>(B, sw, i, 0, rho);
@@ -391,7 +522,6 @@ template <class R, int MODE, bool ENERGY, int TPA>
 __global__ void __launch_bounds__(256) k_force_rows(Bufs<R> B, Geom G, Launch L)
 {
     using R4 = typename V4<R>::T;
-    extern __shared__ __align__(32) unsigned char dyn[];
     R4 *stage = reinterpret_cast<R4 *>(dyn);
     __shared__ R4 sh[27];
     __shared__ int base[9], rstart[9], rcount[9];
@@ -412,11 +542,14 @@ __global__ void __launch_bounds__(256) k_force_rows(Bufs<R> B, Geom G, Launch L)
         const bool active = i < a1;
         R f[3] = {0, 0, 0};
         if (active) {
+            const int nn = B.nnb[i];
+            const ListGlobal list{B.list + i, L.ld};
             if (staged)
-                force_lane<R, false, ENERGY, TPA>(B, L, sh, rc2, s, i, l, 0, stage[i - base[4]],
-                                                  StagedFetch<R>{stage, base}, f, e7);
+                force_lane<R, false, ENERGY, TPA, 4>(B, L, sh, rc2, s, nn, l, 0, stage[i - base[4]], list,
+                                                     StagedFetch<R>{stage, base}, f, e7, TabGlobal<R>{B.coef2});
             else
-                force_lane<R, false, ENERGY, TPA>(B, L, sh, rc2, s, i, l, 0, sw[i], GlobalFetch<R>{sw}, f, e7);
+                force_lane<R, false, ENERGY, TPA, 4>(B, L, sh, rc2, s, nn, l, 0, sw[i], list, GlobalFetch<R>{sw}, f,
+                                                     e7, TabGlobal<R>{B.coef2});
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);
@@ -427,6 +560,88 @@ __global__ void __launch_bounds__(256) k_force_rows(Bufs<R> B, Geom G, Launch L)
     force_block_end<R, ENERGY>(B, L, e7, ke, d2max, MODE == MODE_CLOSE_OPEN);
 }
 
+// ---- spline rows in shared memory (FP32, one atom type, fused tables) ----
+//
+// Persistent blocks: each block copies the f rows (density) or the f and phi
+// rows (force) of the fused table into shared memory once, then walks tiles
+// of blockDim / TPA atoms, tile = blockIdx.x, blockIdx.x + gridDim.x, ...;
+// the grid is what fits on the GPU at once, so there is no partial last wave.
+
+__device__ __forceinline__ void copy_rows(const float4 *coef2, int nint, float4 *f_rows, float4 *phi_rows)
+{
+    for (int k = threadIdx.x; k < nint; k += blockDim.x) {
+        f_rows[k] = coef2[2 * k];
+        if (phi_rows) phi_rows[k] = coef2[2 * k + 1];
+    }
+}
+
+template <bool ENERGY, int TPA>
+__global__ void __launch_bounds__(256) k_density_tab(Bufs<float> B, Geom G, Launch L)
+{
+    float4 *f_rows = reinterpret_cast<float4 *>(dyn);
+    __shared__ float4 sh[27];
+    const int nint = B.tables->fphi.nint;
+    copy_rows(B.coef2, nint, f_rows, nullptr);
+    fill_shift<float>(sh, G);  // ends with a block barrier
+    const DevState *st = B.st;
+    const int sp = st->sp, s = st->set;
+    float4 *sw = B.shadow[sp];
+    const float rc2 = g_rc2<float>(G);
+    const int width = blockDim.x / TPA, l = threadIdx.x % TPA;
+    const int ntiles = (L.n + width - 1) / width;
+    const TabShared tab{f_rows, nullptr};
+    float e_embed = 0.f;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int i = tile * width + threadIdx.x / TPA;
+        const bool active = i < L.n;
+        float rho = 0.f;
+        if (active)
+            rho = density_lane<float, false, TPA, 2>(B, sh, rc2, s, B.nnb[i], l, sw[i], ListGlobal{B.list + i, L.ld},
+                                                     GlobalFetch<float>{sw}, tab);
+        rho = lane_sum<TPA>(rho);
+        if (active && l == 0) e_embed += embed<float>(B, sw, i, 0, rho);
+    }
+    if (ENERGY) {
+        const float v[1] = {e_embed};
+        block_sums_t<1, float>(v, B.partials, L.pstride, 0);
+    }
+}
+
+template <int MODE, bool ENERGY, int TPA>
+__global__ void __launch_bounds__(256) k_force_tab(Bufs<float> B, Geom G, Launch L)
+{
+    const int nint = B.tables->fphi.nint;
+    float4 *f_rows = reinterpret_cast<float4 *>(dyn);
+    float4 *phi_rows = f_rows + nint;
+    __shared__ float4 sh[27];
+    copy_rows(B.coef2, nint, f_rows, phi_rows);
+    fill_shift<float>(sh, G);
+    const DevState *st = B.st;
+    const int sp = st->sp, s = st->set;
+    const float4 *sw = B.shadow[sp];
+    const float rc2 = g_rc2<float>(G);
+    const int width = blockDim.x / TPA, l = threadIdx.x % TPA;
+    const int ntiles = (L.n + width - 1) / width;
+    const TabShared tab{f_rows, phi_rows};
+    float e7[7] = {0, 0, 0, 0, 0, 0, 0};
+    double ke = 0.0;
+    float d2max = 0.f;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int i = tile * width + threadIdx.x / TPA;
+        const bool active = i < L.n;
+        float f[3] = {0, 0, 0};
+        if (active)
+            force_lane<float, false, ENERGY, TPA, 2>(B, L, sh, rc2, s, B.nnb[i], l, 0, sw[i],
+                                                     ListGlobal{B.list + i, L.ld}, GlobalFetch<float>{sw}, f, e7, tab);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);
+        float d2 = 0.f;
+        if (active) integrate<float, MODE, ENERGY, TPA>(B, L, s, sp, i, l, 0, f, ke, d2);
+        d2max = fmaxf(d2max, lane_sum<TPA>(d2));
+    }
+    force_block_end<float, ENERGY>(B, L, e7, ke, d2max, MODE == MODE_CLOSE_OPEN);
+}
+
 // ---- dispatch ----
 
 template <class R, bool MULTI, bool ENERGY>
@@ -434,7 +649,7 @@ void density_tpa(const Bufs<R> &B, const Geom &G, const Launch &L)
 {
     if (!MULTI && L.staged_d) {
         const size_t sm = (size_t)L.stage_cap * sizeof(typename V4<R>::T);
-        dim3 g(L.nrows), b(L.block);
+        dim3 g(L.nrows), b(L.block_d);
         switch (L.tpa_d) {
         case 1: k_density_rows<R, ENERGY, 1><<<g, b, sm, L.stream>>>(B, G, L); break;
         case 2: k_density_rows<R, ENERGY, 2><<<g, b, sm, L.stream>>>(B, G, L); break;
@@ -442,12 +657,33 @@ void density_tpa(const Bufs<R> &B, const Geom &G, const Launch &L)
         }
         return;
     }
-    dim3 g(L.nb_d), b(L.block);
+    if constexpr (std::is_same<R, float>::value && !MULTI) {
+        if (L.tab_d) {
+            const size_t sm = table_smem_bytes(L, false);
+            dim3 g(L.nb_d), b(L.block_d);
+            switch (L.tpa_d) {
+            case 1: k_density_tab<ENERGY, 1><<<g, b, sm, L.stream>>>(B, G, L); break;
+            case 2: k_density_tab<ENERGY, 2><<<g, b, sm, L.stream>>>(B, G, L); break;
+            default: k_density_tab<ENERGY, 4><<<g, b, sm, L.stream>>>(B, G, L); break;
+            }
+            return;
+        }
+    }
+    dim3 g(L.nb_d), b(L.block_d);
+    if (!MULTI && L.tiled_d && list_tile_bytes(L, L.tpa_d, L.block_d) <= (size_t)kSharedLimitBytes) {
+        const size_t sm = list_tile_bytes(L, L.tpa_d, L.block_d);
+        switch (L.tpa_d) {
+        case 1: k_density<R, MULTI, ENERGY, 1, true><<<g, b, sm, L.stream>>>(B, G, L); break;
+        case 2: k_density<R, MULTI, ENERGY, 2, true><<<g, b, sm, L.stream>>>(B, G, L); break;
+        default: k_density<R, MULTI, ENERGY, 4, true><<<g, b, sm, L.stream>>>(B, G, L); break;
+        }
+        return;
+    }
     switch (L.tpa_d) {
-    case 1: k_density<R, MULTI, ENERGY, 1><<<g, b, 0, L.stream>>>(B, G, L); break;
-    case 2: k_density<R, MULTI, ENERGY, 2><<<g, b, 0, L.stream>>>(B, G, L); break;
-    case 4: k_density<R, MULTI, ENERGY, 4><<<g, b, 0, L.stream>>>(B, G, L); break;
-    default: k_density<R, MULTI, ENERGY, 8><<<g, b, 0, L.stream>>>(B, G, L); break;
+    case 1: k_density<R, MULTI, ENERGY, 1, false><<<g, b, 0, L.stream>>>(B, G, L); break;
+    case 2: k_density<R, MULTI, ENERGY, 2, false><<<g, b, 0, L.stream>>>(B, G, L); break;
+    case 4: k_density<R, MULTI, ENERGY, 4, false><<<g, b, 0, L.stream>>>(B, G, L); break;
+    default: k_density<R, MULTI, ENERGY, 8, false><<<g, b, 0, L.stream>>>(B, G, L); break;
     }
 }
 
@@ -456,7 +692,7 @@ void force_tpa(const Bufs<R> &B, const Geom &G, const Launch &L)
 {
     if (!MULTI && L.staged_f) {
         const size_t sm = (size_t)L.stage_cap * sizeof(typename V4<R>::T);
-        dim3 g(L.nrows), b(L.block);
+        dim3 g(L.nrows), b(L.block_f);
         switch (L.tpa_f) {
         case 1: k_force_rows<R, MODE, ENERGY, 1><<<g, b, sm, L.stream>>>(B, G, L); break;
         case 2: k_force_rows<R, MODE, ENERGY, 2><<<g, b, sm, L.stream>>>(B, G, L); break;
@@ -464,12 +700,33 @@ void force_tpa(const Bufs<R> &B, const Geom &G, const Launch &L)
         }
         return;
     }
-    dim3 g(L.nb_f), b(L.block);
+    if constexpr (std::is_same<R, float>::value && !MULTI) {
+        if (L.tab_f) {
+            const size_t sm = table_smem_bytes(L, true);
+            dim3 g(L.nb_f), b(L.block_f);
+            switch (L.tpa_f) {
+            case 1: k_force_tab<MODE, ENERGY, 1><<<g, b, sm, L.stream>>>(B, G, L); break;
+            case 2: k_force_tab<MODE, ENERGY, 2><<<g, b, sm, L.stream>>>(B, G, L); break;
+            default: k_force_tab<MODE, ENERGY, 4><<<g, b, sm, L.stream>>>(B, G, L); break;
+            }
+            return;
+        }
+    }
+    dim3 g(L.nb_f), b(L.block_f);
+    if (!MULTI && L.tiled_f && list_tile_bytes(L, L.tpa_f, L.block_f) <= (size_t)kSharedLimitBytes) {
+        const size_t sm = list_tile_bytes(L, L.tpa_f, L.block_f);
+        switch (L.tpa_f) {
+        case 1: k_force<R, MULTI, MODE, ENERGY, 1, true><<<g, b, sm, L.stream>>>(B, G, L); break;
+        case 2: k_force<R, MULTI, MODE, ENERGY, 2, true><<<g, b, sm, L.stream>>>(B, G, L); break;
+        default: k_force<R, MULTI, MODE, ENERGY, 4, true><<<g, b, sm, L.stream>>>(B, G, L); break;
+        }
+        return;
+    }
     switch (L.tpa_f) {
-    case 1: k_force<R, MULTI, MODE, ENERGY, 1><<<g, b, 0, L.stream>>>(B, G, L); break;
-    case 2: k_force<R, MULTI, MODE, ENERGY, 2><<<g, b, 0, L.stream>>>(B, G, L); break;
-    case 4: k_force<R, MULTI, MODE, ENERGY, 4><<<g, b, 0, L.stream>>>(B, G, L); break;
-    default: k_force<R, MULTI, MODE, ENERGY, 8><<<g, b, 0, L.stream>>>(B, G, L); break;
+    case 1: k_force<R, MULTI, MODE, ENERGY, 1, false><<<g, b, 0, L.stream>>>(B, G, L); break;
+    case 2: k_force<R, MULTI, MODE, ENERGY, 2, false><<<g, b, 0, L.stream>>>(B, G, L); break;
+    case 4: k_force<R, MULTI, MODE, ENERGY, 4, false><<<g, b, 0, L.stream>>>(B, G, L); break;
+    default: k_force<R, MULTI, MODE, ENERGY, 8, false><<<g, b, 0, L.stream>>>(B, G, L); break;
     }
 }
 
@@ -489,6 +746,43 @@ void force_modes(const Bufs<R> &B, const Geom &G, const Launch &L, int mode, boo
 }
 
 // Shared-memory opt-in of the row-staged kernels for `bytes` of stage.
+template <class K>
+cudaError_t allow_bytes(K kernel, int bytes)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <class R, int MODE, bool ENERGY>
+cudaError_t allow_tiled_force(int bytes)
+{
+    cudaError_t e = allow_bytes(k_force<R, false, MODE, ENERGY, 1, true>, bytes);
+    if (e == cudaSuccess) e = allow_bytes(k_force<R, false, MODE, ENERGY, 2, true>, bytes);
+    if (e == cudaSuccess) e = allow_bytes(k_force<R, false, MODE, ENERGY, 4, true>, bytes);
+    return e;
+}
+
+template <class R, bool ENERGY>
+cudaError_t allow_tiled_density(int bytes)
+{
+    cudaError_t e = allow_bytes(k_density<R, false, ENERGY, 1, true>, bytes);
+    if (e == cudaSuccess) e = allow_bytes(k_density<R, false, ENERGY, 2, true>, bytes);
+    if (e == cudaSuccess) e = allow_bytes(k_density<R, false, ENERGY, 4, true>, bytes);
+    return e;
+}
+
+template <int MODE>
+cudaError_t allow_tab_force(int bytes)
+{
+    cudaError_t e = cudaSuccess;
+    for (int t : {1, 2, 4}) {
+        if (e != cudaSuccess) break;
+        e = allow_bytes(t == 1 ? k_force_tab<MODE, false, 1> : (t == 2 ? k_force_tab<MODE, false, 2> : k_force_tab<MODE, false, 4>), bytes);
+        if (e == cudaSuccess)
+            e = allow_bytes(t == 1 ? k_force_tab<MODE, true, 1> : (t == 2 ? k_force_tab<MODE, true, 2> : k_force_tab<MODE, true, 4>), bytes);
+    }
+    return e;
+}
+
 template <class R, int MODE, bool ENERGY>
 cudaError_t allow_rows_force(int bytes)
 {
@@ -534,8 +828,26 @@ int launch_force(const Bufs<R> &B, const Geom &G, const Launch &L, int mode, boo
     return 1;
 }
 
+// Resident blocks per SM of the shared-table passes (the hot force variant).
+inline int table_blocks_per_sm(const Launch &L, bool force, int tpa, int block)
+{
+    int nb = 0;
+    const size_t sm = table_smem_bytes(L, force);
+    cudaError_t e;
+    if (force)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, tpa == 1 ? k_force_tab<MODE_CLOSE_OPEN, false, 1>
+                          : (tpa == 2 ? k_force_tab<MODE_CLOSE_OPEN, false, 2> : k_force_tab<MODE_CLOSE_OPEN, false, 4>),
+            block, sm);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, tpa == 1 ? k_density_tab<false, 1> : (tpa == 2 ? k_density_tab<false, 2> : k_density_tab<false, 4>),
+            block, sm);
+    return e == cudaSuccess ? nb : 0;
+}
+
 template <class R>
-cudaError_t allow_row_staging(int bytes)
+cudaError_t allow_shared_staging(int bytes)
 {
     cudaError_t e = allow_rows_density<R, false>(bytes);
     if (e == cudaSuccess) e = allow_rows_density<R, true>(bytes);
@@ -545,7 +857,27 @@ cudaError_t allow_row_staging(int bytes)
     if (e == cudaSuccess) e = allow_rows_force<R, MODE_CLOSE, true>(bytes);
     if (e == cudaSuccess) e = allow_rows_force<R, MODE_CLOSE_OPEN, false>(bytes);
     if (e == cudaSuccess) e = allow_rows_force<R, MODE_CLOSE_OPEN, true>(bytes);
+    if (e == cudaSuccess) e = allow_tiled_density<R, false>(bytes);
+    if (e == cudaSuccess) e = allow_tiled_density<R, true>(bytes);
+    if (e == cudaSuccess) e = allow_tiled_force<R, MODE_MEASURE, false>(bytes);
+    if (e == cudaSuccess) e = allow_tiled_force<R, MODE_MEASURE, true>(bytes);
+    if (e == cudaSuccess) e = allow_tiled_force<R, MODE_CLOSE, false>(bytes);
+    if (e == cudaSuccess) e = allow_tiled_force<R, MODE_CLOSE, true>(bytes);
+    if (e == cudaSuccess) e = allow_tiled_force<R, MODE_CLOSE_OPEN, false>(bytes);
+    if (e == cudaSuccess) e = allow_tiled_force<R, MODE_CLOSE_OPEN, true>(bytes);
+    if constexpr (std::is_same<R, float>::value) {
+        for (int t : {1, 2, 4}) {
+            if (e != cudaSuccess) break;
+            e = allow_bytes(t == 1 ? k_density_tab<false, 1> : (t == 2 ? k_density_tab<false, 2> : k_density_tab<false, 4>), bytes);
+            if (e == cudaSuccess)
+                e = allow_bytes(t == 1 ? k_density_tab<true, 1> : (t == 2 ? k_density_tab<true, 2> : k_density_tab<true, 4>), bytes);
+        }
+        if (e == cudaSuccess) e = allow_tab_force<MODE_MEASURE>(bytes);
+        if (e == cudaSuccess) e = allow_tab_force<MODE_CLOSE>(bytes);
+        if (e == cudaSuccess) e = allow_tab_force<MODE_CLOSE_OPEN>(bytes);
+    }
     return e;
 }
+
 
 }  // namespace eammd

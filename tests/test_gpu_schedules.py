@@ -1,11 +1,13 @@
-"""The row-staged schedule of the density and force passes against the
-atom-parallel one and the serial FP64 oracle.
+"""The row-staged and list-tiled schedules of the density and force passes
+against the atom-parallel one and the serial FP64 oracle.
 
 A row-staged block copies the neighbour records of the 3 x 3 rows of cells
-around its row into shared memory and gathers from there; the per-atom sums
-run in the same order as in the atom-parallel passes with the same lanes per
-atom, so forces and trajectories must agree bitwise, and both must meet the
-oracle bars (FP64 1e-10, mixed 2e-5, relative 2-norm over all 3N components).
+around its row into shared memory and gathers from there; a list-tiled block
+bulk-copies its atoms' list columns into shared memory first.  The per-atom
+sums run in the same order as in the atom-parallel passes with the same lanes
+per atom, so forces and trajectories must agree bitwise, and all must meet
+the oracle bars (FP64 1e-10, mixed 2e-5, relative 2-norm over all 3N
+components).
 """
 import numpy as np
 import pytest
@@ -16,6 +18,7 @@ from paper_2405_07898_gb300 import binding, inputs as I
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-10, "mixed": 2e-5}
+FLAGS = ("rows_density", "rows_force", "tiles_density", "tiles_force", "table_density", "table_force")
 
 
 def rel(a, b):
@@ -62,15 +65,22 @@ def c1():
     return I.bcc_2000_fp64()
 
 
+@pytest.mark.parametrize("schedule", ["rows", "tiles", "table"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("lanes", [1, 2, 4])
-def test_rows_equal_atoms_and_oracle(c1, precision, lanes):
+def test_schedule_equals_atoms_and_oracle(c1, schedule, precision, lanes):
     _, _, F, E, W = oracle_eval(c1)
     kw = dict(precision=precision, lanes_per_atom=lanes)
-    with binding.MD(c1, schedule="rows", **kw) as a, binding.MD(c1, schedule="atoms", **kw) as b:
+    with binding.MD(c1, schedule=schedule, **kw) as a, binding.MD(c1, schedule="atoms", **kw) as b:
         sa, sb = a.stats(), b.stats()
-        assert sa["rows_density"] == sa["rows_force"] == 1 and sa["stage_capacity"] > 0
-        assert sb["rows_density"] == sb["rows_force"] == 0
+        if schedule == "rows":
+            assert sa["rows_density"] == sa["rows_force"] == 1 and sa["stage_capacity"] > 0
+        elif schedule == "tiles":
+            assert sa["tiles_density"] == sa["tiles_force"] == 1
+        else:  # FP32 only; the FP64 path falls back to the atom-parallel passes
+            assert sa["table_density"] == sa["table_force"] == (1 if precision == "mixed" else 0)
+        for k in FLAGS:
+            assert sb[k] == 0
         np.testing.assert_array_equal(a.forces(), b.forces())
         assert rel(a.forces(), F) < TOL[precision]
         pe, _ = a.energy()
@@ -89,7 +99,7 @@ def test_rows_equal_atoms_and_oracle(c1, precision, lanes):
         ea, eb = sum(a.energy()), sum(b.energy())
         assert abs(ea - eb) / abs(eb) < (1e-13 if precision == "fp64" else 1e-9)
     _, _, F2, _, _ = oracle_eval(c1, pa)
-    with binding.MD(c1, schedule="rows", **kw) as c:
+    with binding.MD(c1, schedule=schedule, **kw) as c:
         c.set_state(pa, va, 37)
         assert rel(c.forces(), F2) < TOL[precision]
 
@@ -121,21 +131,43 @@ def test_rows_with_blocks_past_the_stage(precision):
             assert rel(a.forces(), F2) < TOL[precision]
 
 
+@pytest.mark.parametrize("schedule", ["tiles", "table"])
+def test_uneven_cells_and_ragged_tail(schedule):
+    """List tiles and shared-table passes on the random gas (uneven neighbour
+    counts; the last tile holds a ragged tail of atoms): bitwise equal to the
+    atom-parallel passes."""
+    s = random_gas()
+    for precision in ("fp64", "mixed"):
+        for lanes in (1, 4):
+            kw = dict(precision=precision, lanes_per_atom=lanes)
+            with binding.MD(s, schedule=schedule, **kw) as a, binding.MD(s, schedule="atoms", **kw) as b:
+                assert a.n % (256 // lanes) != 0
+                np.testing.assert_array_equal(a.forces(), b.forces())
+                a.step(25, 1.0)
+                b.step(25, 1.0)
+                np.testing.assert_array_equal(a.get_state()[0], b.get_state()[0])
+                np.testing.assert_array_equal(a.forces(), b.forces())
+
+
 def test_rows_rejections_and_multi_type_fallback():
     s = I.bcc_2000_fp64()
-    with pytest.raises(binding.MDError) as e:
-        binding.MD(s, schedule="rows", lanes_per_atom=8)
-    assert e.value.status == -1
+    for sched in ("rows", "tiles", "table"):
+        with pytest.raises(binding.MDError) as e:
+            binding.MD(s, schedule=sched, lanes_per_atom=8)
+        assert e.value.status == -1
     with pytest.raises(binding.MDError) as e:
         binding.MD(s, schedule="rows", precision="fp64", stage_capacity=1 << 20)
     assert e.value.status == -1
     # two atom types: the type-dependent path has no row-staged form
     m = I.multi_type_system()
     _, _, F, _, _ = oracle_eval(m)
-    with binding.MD(m, precision="fp64", schedule="rows", lanes_per_atom=2) as md:
-        st = md.stats()
-        assert st["rows_density"] == st["rows_force"] == 0
-        assert rel(md.forces(), F) < TOL["fp64"]
+    for sched in ("rows", "tiles", "table"):
+        for precision in ("fp64", "mixed"):
+            with binding.MD(m, precision=precision, schedule=sched, lanes_per_atom=2) as md:
+                st = md.stats()
+                for k in FLAGS:
+                    assert st[k] == 0
+                assert rel(md.forces(), F) < TOL[precision]
 
 
 def test_autotuned_schedule_is_deterministic():
@@ -148,5 +180,21 @@ def test_autotuned_schedule_is_deterministic():
             md.step(20, 2.0)
             out.append((md.get_state()[0], md.stats()))
     np.testing.assert_array_equal(out[0][0], out[1][0])
-    for k in ("lanes_density", "lanes_force", "rows_density", "rows_force"):
+    for k in ("lanes_density", "lanes_force", "threads_density", "threads_force") + FLAGS:
         assert out[0][1][k] == out[1][1][k]
+
+
+@pytest.mark.parametrize("block", [96, 160, 224])
+def test_block_sizes_give_the_same_forces(c1, block):
+    """Threads per block change only the block partition of the energy sums:
+    forces and trajectories are bitwise those of 256-thread blocks."""
+    for precision in ("fp64", "mixed"):
+        kw = dict(precision=precision, lanes_per_atom=2, schedule="atoms")
+        with binding.MD(c1, block_size=block, **kw) as a, binding.MD(c1, block_size=256, **kw) as b:
+            assert a.stats()["threads_force"] == block
+            np.testing.assert_array_equal(a.forces(), b.forces())
+            a.step(23, 2.0)
+            b.step(23, 2.0)
+            np.testing.assert_array_equal(a.get_state()[0], b.get_state()[0])
+            ea, eb = sum(a.energy()), sum(b.energy())
+            assert abs(ea - eb) / abs(eb) < (1e-13 if precision == "fp64" else 1e-9)
