@@ -353,6 +353,44 @@ __device__ __forceinline__ void force_block_end(const Bufs<R> &B, const Launch &
     if (open) block_max_disp(d2max, &B.st->maxdisp2);
 }
 
+// ---- L2 prefetch of a warp's streams ----
+
+constexpr bool kPrefetchWarpStreams = true;
+
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)));
+}
+
+// Ask L2 for the lines a warp of the atom-parallel passes streams from
+// device memory, atoms [a0, a0 + m): the list columns up to the longest list
+// of the last build and, in the force pass, the velocities, displacements
+// and reference coordinates its integration reads.  A hint: nothing waits on
+// it, and every address lies inside its array.
+template <class R, bool FORCE>
+__device__ __forceinline__ void prefetch_warp_streams(const Bufs<R> &B, const Launch &L, int s, int a0, int m,
+                                                      int ncol)
+{
+    if (!kPrefetchWarpStreams || a0 >= L.n) return;
+    const int lane = threadIdx.x & 31;
+    for (int k = lane; k < ncol; k += 32) prefetch_l2(B.list + (size_t)k * L.ld + a0);
+    if (FORCE) {
+        // 128-byte lines: 16 doubles or 128 / sizeof(R) reference coordinates
+        const int last = min(a0 + m, L.n) - 1;
+        const int k = lane;
+        if (k < 6) {
+            const int c = k % 3;
+            const int a = (k < 3) ? a0 : min(a0 + 16, last);
+            prefetch_l2(B.v[s][c] + a);
+            prefetch_l2(B.d[c] + a);
+        } else if (k < 9) {
+            prefetch_l2(B.uref[k - 6] + a0);
+        } else if (k < 12 && sizeof(R) == 8) {
+            prefetch_l2(B.uref[k - 9] + min(a0 + 16, last));
+        }
+    }
+}
+
 // ---- atom-parallel schedule ----
 
 // Pairs in flight per lane: the type-dependent path needs more registers a pair.
@@ -378,6 +416,7 @@ __global__ void __launch_bounds__(256) k_density(Bufs<R> B, Geom G, Launch L)
     const int width = blockDim.x / TPA;
     const int i0 = blockIdx.x * width;
     uint32_t *tile = reinterpret_cast<uint32_t *>(dyn);
+    if (!LS) prefetch_warp_streams<R, false>(B, L, s, i0 + (threadIdx.x >> 5) * (32 / TPA), 32 / TPA, min(st->max_nnb, L.cap));
     const bool tiled = LS && stage_list(B.list, L.ld, i0, width, min(st->max_nnb, L.cap), tile, &B.st->error);
     const int i = i0 + threadIdx.x / TPA, l = threadIdx.x % TPA;
     const bool active = i < L.n;
@@ -415,6 +454,7 @@ __global__ void __launch_bounds__(256) k_force(Bufs<R> B, Geom G, Launch L)
     const int width = blockDim.x / TPA;
     const int i0 = blockIdx.x * width;
     uint32_t *tile = reinterpret_cast<uint32_t *>(dyn);
+    prefetch_warp_streams<R, true>(B, L, s, i0 + (threadIdx.x >> 5) * (32 / TPA), 32 / TPA, LS ? 0 : min(st->max_nnb, L.cap));
     const bool tiled = LS && stage_list(B.list, L.ld, i0, width, min(st->max_nnb, L.cap), tile, &B.st->error);
     const int i = i0 + threadIdx.x / TPA, l = threadIdx.x % TPA;
     const bool active = i < L.n;
