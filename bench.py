@@ -156,11 +156,15 @@ def run_ours(args):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    if args.profiler_range:
+        torch.cuda.profiler.start()
     e0.record(stream)
     for _ in range(args.steps):
         bench_step()
     e1.record(stream)
     md.sync()
+    if args.profiler_range:
+        torch.cuda.profiler.stop()
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms_total = e0.elapsed_time(e1)
@@ -329,20 +333,31 @@ def run_drift(args):
     print(json.dumps({"workload": "nve_drift", "runs": out}), flush=True)
 
 
+TRAFFIC_SOURCES = ("pair_kernels.cuh", "device_common.cuh", "md_internal.cuh", "pair_f32.cu")
+
+
+def kernel_source_sha256():
+    """Hash of the sources the force kernel is compiled from."""
+    import hashlib
+    from paper_2405_07898_gb300 import build
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(build.CSRC, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def load_traffic():
     """DRAM bytes per force launch from the committed ncu summary, if the
-    kernel has not changed since it was taken (else null)."""
+    kernel sources have not changed since it was taken (else null)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as fh:
             t = json.load(fh)
-        from paper_2405_07898_gb300 import build
-        import hashlib
-        src = open(os.path.join(build.CSRC, "kernels.cu"), "rb").read()
-        if t.get("kernels_sha256") != hashlib.sha256(src).hexdigest():
+        if t.get("source_sha256") != kernel_source_sha256():
             return None
         return t.get("force_dram_bytes_per_launch")
-    except Exception:
+    except (OSError, ValueError):
         return None
 
 
@@ -417,6 +432,8 @@ def main():
     ap.add_argument("--drift-steps", type=int, default=100000)
     ap.add_argument("--cells", type=int, nargs=3, default=None,
                     help="BCC cells per axis of a smaller profiling case (default: the 74x74x73 workload)")
+    ap.add_argument("--profiler-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--eager", action="store_true",
                     help="launch the step kernels one by one instead of replaying CUDA graphs "
                          "(same kernels; lets a profiler list every launch)")

@@ -164,7 +164,7 @@ void md_options_default(md_options *opt);
  * Builds the tables, bins the atoms, builds the list and evaluates the
  * forces, energies and virial of the initial state.  Synchronises.
  * Errors: MD_ERR_ARG, MD_ERR_BOX, MD_ERR_NONFINITE, MD_ERR_OOM, MD_ERR_CUDA,
- * MD_ERR_CAPACITY (n >= 2^27). */
+ * MD_ERR_CAPACITY (n >= 2^26). */
 md_status md_create(const double box[3], int64_t n, const double *pos, const double *vel,
                     const int32_t *types, const md_potential *pot, const md_options *opt,
                     md_ctx **out);

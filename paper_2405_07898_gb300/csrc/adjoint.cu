@@ -111,8 +111,8 @@ __global__ void k_adj_g(Bufs<double> B, const double *f_ref, double *g, int n, d
 __global__ void k_adj_rho(Bufs<double> B, Geom G, int n, int ld, AdjDesc D, int off_f, int off_F, const double *g,
                           double *rho_out, double *drho_out)
 {
-    __shared__ double4_32a sh[27];
-    fill_shift<double>(sh, G);
+    double h[3];
+    load_h<double>(G, h);
     const int sp = B.st->sp;
     const double4_32a *sw = B.shadow[sp];
     int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -125,7 +125,7 @@ __global__ void k_adj_rho(Bufs<double> B, Geom G, int n, int ld, AdjDesc D, int 
         uint32_t e = B.list[(size_t)k * ld + p];
         int j = (int)(e & kIndexMask);
         double4_32a uj = sw[j];
-        double4_32a s = sh[e >> kCodeShift];
+        const Shift<double> s = entry_shift<double>(e, h);
         double dx = (uj.x - ui.x) + s.x, dy = (uj.y - ui.y) + s.y, dz = (uj.z - ui.z) + s.z;
         double r2 = dx * dx + dy * dy + dz * dz;
         if (!(r2 < G.rc2)) continue;
@@ -145,13 +145,10 @@ __global__ void k_adj_accum(Bufs<double> B, Geom G, int n, int ld, AdjDesc D, in
                             const double *rho_in, const double *drho_in, double *block_bins)
 {
     extern __shared__ double bins[];
-    __shared__ double4_32a sh[27];
     const int lane = threadIdx.x;
     for (int r = lane; r < 4 * D.nrows; r += 32) bins[r] = 0.0;
-    for (int c = lane; c < 27; c += 32) {
-        int dx = c % 3 - 1, dy = (c / 3) % 3 - 1, dz = c / 9 - 1;
-        sh[c] = make_double4_32a(dx * G.h[0], dy * G.h[1], dz * G.h[2], 0.0);
-    }
+    double h[3];
+    load_h<double>(G, h);
     __syncwarp();
     const int sp = B.st->sp;
     const double4_32a *sw = B.shadow[sp];
@@ -188,7 +185,7 @@ __global__ void k_adj_accum(Bufs<double> B, Geom G, int n, int ld, AdjDesc D, in
             uint32_t e = B.list[(size_t)k * ld + p];
             int j = (int)(e & kIndexMask);
             double4_32a uj = sw[j];
-            double4_32a s = sh[e >> kCodeShift];
+            const Shift<double> s = entry_shift<double>(e, h);
             double dx = (uj.x - ui.x) + s.x, dy = (uj.y - ui.y) + s.y, dz = (uj.z - ui.z) + s.z;
             double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < G.rc2) {

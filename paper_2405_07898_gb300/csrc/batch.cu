@@ -345,7 +345,8 @@ __device__ void rb_list(const BatchBufs &B, Smem &S, int set, int sp, int cap, R
                     if (in) {
                         const int pos = cnt0 + __popc(mask & lt);
                         if (pos < cap)
-                            B.list[P.list_off + (size_t)pos * P.ld + p] = (uint32_t)q | ((uint32_t)code << kCodeShift);
+                            B.list[P.list_off + (size_t)pos * P.ld + p] =
+                                list_entry((uint32_t)q, code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1);
                     }
                     if (lane == a) my_cnt += __popc(mask);
                 }
@@ -373,6 +374,7 @@ __device__ void run_replica(const BatchBufs &B, Smem &S, int r, int mode, int ns
     const SplineDesc<float> Fd = B.Fd[P.pot];
     const double hk = P.kick_per_dt * dt;  // F dt / (2m) per unit force
     const float hkf = (float)hk;
+    const float hf[3] = {P.h_f[0], P.h_f[1], P.h_f[2]};
     int set = st->set, sp = st->sp, since = st->since_build;
     float maxd2 = st->maxdisp2;
     const int steps = (mode == BATCH_INIT) ? 1 : nsteps;
@@ -434,7 +436,7 @@ __device__ void run_replica(const BatchBufs &B, Smem &S, int r, int mode, int ns
             for (int k = 0; k < nn; ++k) {
                 const uint32_t e = lp[(size_t)k * P.ld];
                 const float4 uj = sw[e & kIndexMask];
-                const float4 shf = S.shift[e >> kCodeShift];
+                const Shift<float> shf = entry_shift<float>(e, hf);
                 const float dx = (uj.x - ui.x) + shf.x, dy = (uj.y - ui.y) + shf.y, dz = (uj.z - ui.z) + shf.z;
                 const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                 if (r2 < P.rc2_f) {
@@ -466,7 +468,7 @@ __device__ void run_replica(const BatchBufs &B, Smem &S, int r, int mode, int ns
             for (int k = 0; k < nn; ++k) {
                 const uint32_t e = lp[(size_t)k * P.ld];
                 const float4 uj = sw[e & kIndexMask];
-                const float4 shf = S.shift[e >> kCodeShift];
+                const Shift<float> shf = entry_shift<float>(e, hf);
                 const float dx = (uj.x - ui.x) + shf.x, dy = (uj.y - ui.y) + shf.y, dz = (uj.z - ui.z) + shf.z;
                 const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                 if (r2 < P.rc2_f) {
@@ -804,7 +806,7 @@ md_status md_batch_create(int32_t nrep, const md_replica *reps, int32_t npot, co
     }
     if (atom_off >= (int64_t)kIndexMask) {
         delete b;
-        return bad(MD_ERR_CAPACITY, "more than 2^27 atoms in all");
+        return bad(MD_ERR_CAPACITY, "more than 2^26 atoms in all");
     }
     b->total = atom_off;
     const int cap = o.list_capacity > 0 ? o.list_capacity : std::max(16, ((int)std::ceil(1.25 * max_expect) + 8 + 3) & ~3);

@@ -111,16 +111,36 @@ template <class R> __device__ __forceinline__ R g_screen_hi(const Geom &G);
 template <> __device__ __forceinline__ float g_screen_hi<float>(const Geom &G) { return G.screen_hi_f; }
 template <> __device__ __forceinline__ double g_screen_hi<double>(const Geom &G) { return G.screen_hi; }
 
-// Shift of the 27 stencil cells, code = (dz+1)*9 + (dy+1)*3 + (dx+1):
-// u_j + shift(code) - u_i is the displacement x_j - x_i of a listed pair.
+// Shift of a list entry's stencil cell: u_j + shift - u_i is the
+// displacement x_j - x_i of the pair.  Per axis -h, 0 or h from the entry's
+// 2-bit field (the same values as (R)d * h for d = -1, 0, 1), so the kernels
+// keep no table of shifts.
+template <class R> struct Shift {
+    R x, y, z;
+};
 template <class R>
-__device__ __forceinline__ void fill_shift(typename V4<R>::T *sh, const Geom &G)
+__device__ __forceinline__ R axis_shift(uint32_t e, int axis, R h)
 {
-    for (int c = threadIdx.x; c < 27; c += blockDim.x) {
-        int dx = c % 3 - 1, dy = (c / 3) % 3 - 1, dz = c / 9 - 1;
-        sh[c] = mk4<R>((R)dx * g_h<R>(G, 0), (R)dy * g_h<R>(G, 1), (R)dz * g_h<R>(G, 2), (R)0);
-    }
-    __syncthreads();
+    const uint32_t t = (e >> (kCodeShift + 2 * axis)) & 3u;
+    return t == 1u ? (R)0 : (t == 0u ? -h : h);
+}
+template <class R>
+__device__ __forceinline__ Shift<R> entry_shift(uint32_t e, const R (&h)[3])
+{
+    return Shift<R>{axis_shift<R>(e, 0, h[0]), axis_shift<R>(e, 1, h[1]), axis_shift<R>(e, 2, h[2])};
+}
+// Row (dz + 1) * 3 + (dy + 1) of the 3 x 3 rows of cells around an atom's
+// row that a list entry's neighbour lives in.
+__device__ __forceinline__ int entry_row(uint32_t e)
+{
+    return (int)(e >> (kCodeShift + 4)) * 3 + (int)((e >> (kCodeShift + 2)) & 3u);
+}
+template <class R>
+__device__ __forceinline__ void load_h(const Geom &G, R (&h)[3])
+{
+    h[0] = g_h<R>(G, 0);
+    h[1] = g_h<R>(G, 1);
+    h[2] = g_h<R>(G, 2);
 }
 
 // Error-free sum of two floats (Knuth's TwoSum): a + b = s + e exactly.

@@ -993,7 +993,7 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     if (!out) return bad(MD_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!box || !pot || n < 0 || (n > 0 && (!pos || !types))) return bad(MD_ERR_ARG, "null argument or n < 0");
-    if (n >= (int64_t)kIndexMask) return bad(MD_ERR_CAPACITY, "n must be below 2^27");
+    if (n >= (int64_t)kIndexMask) return bad(MD_ERR_CAPACITY, "n must be below 2^26");
     if (pot->ntypes < 1 || pot->ntypes > kMaxTypes || !pot->mass || !pot->F || !pot->f || !pot->phi)
         return bad(MD_ERR_ARG, "potential: ntypes must be 1..8 and all tables given");
     if (!(pot->r_cut > 0.0) || !(pot->skin >= 0.0) || !std::isfinite(pot->r_cut) || !std::isfinite(pot->skin))

@@ -14,7 +14,9 @@
 //                across steps
 //   fcache[3]    R SoA, forces of the last closed step
 //   list         uint32 [capacity][ld] (column k of atom i at k*ld + i):
-//                neighbour index in bits 0..26, stencil code in bits 27..31
+//                neighbour index in bits 0..25; the stencil offset (dx, dy,
+//                dz) of the neighbour's cell as t = d + 1 in {0, 1, 2} in
+//                bits 26..27 (x), 28..29 (y), 30..31 (z)
 //   nnb          int32 neighbours per atom
 // "set" flips at every list build (the permutation writes the other set),
 // "sp" flips at every drift.  Both live in DevState, on the device, so that a
@@ -28,8 +30,14 @@ namespace eammd {
 
 constexpr int kMaxTypes = 8;
 constexpr int kMaxPairs = kMaxTypes * (kMaxTypes + 1) / 2;
-constexpr int kCodeShift = 27;
+constexpr int kCodeShift = 26;
 constexpr uint32_t kIndexMask = (1u << kCodeShift) - 1u;
+
+// List entry of neighbour q in the stencil cell at offset (dx, dy, dz).
+__host__ __device__ constexpr uint32_t list_entry(uint32_t q, int dx, int dy, int dz)
+{
+    return q | ((uint32_t)((dx + 1) | ((dy + 1) << 2) | ((dz + 1) << 4)) << kCodeShift);
+}
 constexpr int kScanBlock = 1024;
 constexpr int kEnergySlots = 10;  // embed, pair, ke, virial xx yy zz xy xz yz, spare
 constexpr double kAccel = 9.648533215665e-3;  // (eV/Angstrom/amu) -> Angstrom/fs^2

@@ -32,7 +32,7 @@ template <class R> struct PairIn {
 
 template <class R>
 __device__ __forceinline__ PairIn<R> pair_vector(const typename V4<R>::T &ui, const typename V4<R>::T &uj,
-                                                 const typename V4<R>::T &shf)
+                                                 const Shift<R> &shf)
 {
     PairIn<R> p;
     p.dx = (uj.x - ui.x) + shf.x;
@@ -77,11 +77,10 @@ struct GlobalFetch {
 template <class R>
 struct StagedFetch {
     const typename V4<R>::T *stage;
-    const int *base;  // per neighbour row t = code / 3: first atom index minus its stage offset
+    const int *base;  // per neighbour row (entry_row): first atom index minus its stage offset
     __device__ __forceinline__ typename V4<R>::T operator()(uint32_t e) const
     {
-        const int t = (int)(e >> kCodeShift) / 3;
-        return stage[(int)(e & kIndexMask) - base[t]];
+        return stage[(int)(e & kIndexMask) - base[entry_row(e)]];
     }
 };
 
@@ -184,7 +183,7 @@ __device__ __forceinline__ bool stage_list(const uint32_t *list, int ld, int i0,
 // This lane's part of rho_i = sum over listed j with r < r_cut of f_{t_j}(r_ij)
 // (Eq. 2).
 template <class R, bool MULTI, int TPA, int U, class List, class Fetch, class Tab>
-__device__ __forceinline__ R density_lane(const Bufs<R> &B, const typename V4<R>::T *sh, R rc2, int s, int nn,
+__device__ __forceinline__ R density_lane(const Bufs<R> &B, const R (&h)[3], R rc2, int s, int nn,
                                           int l, const typename V4<R>::T &ui, const List &list, const Fetch &fetch,
                                           const Tab &tab)
 {
@@ -203,7 +202,7 @@ __device__ __forceinline__ R density_lane(const Bufs<R> &B, const typename V4<R>
         for (int q = 0; q < U; ++q) u[q] = fetch(q == 0 || k + q * TPA < nn ? e[q] : e[0]);
 #pragma unroll
         for (int q = 0; q < U; ++q) {
-            const PairIn<R> p = pair_vector<R>(ui, u[q], sh[e[q] >> kCodeShift]);
+            const PairIn<R> p = pair_vector<R>(ui, u[q], entry_shift<R>(e[q], h));
             if ((q == 0 || k + q * TPA < nn) && p.r2 < rc2) {
                 R rinv, r;
                 inv_r(p.r2, rinv, r);
@@ -242,7 +241,7 @@ __device__ __forceinline__ R embed(const Bufs<R> &B, typename V4<R>::T *sw, int 
 // and, when ENERGY, of the pair energy and the virial (e7: pair energy, then
 // W xx yy zz xy xz yz).
 template <class R, bool MULTI, bool ENERGY, int TPA, int U, class List, class Fetch, class Tab>
-__device__ __forceinline__ void force_lane(const Bufs<R> &B, const Launch &L, const typename V4<R>::T *sh, R rc2,
+__device__ __forceinline__ void force_lane(const Bufs<R> &B, const Launch &L, const R (&h)[3], R rc2,
                                            int s, int nn, int l, int ti, const typename V4<R>::T &ui,
                                            const List &list, const Fetch &fetch, R (&f)[3], R (&e7)[7],
                                            const Tab &tab)
@@ -260,7 +259,7 @@ __device__ __forceinline__ void force_lane(const Bufs<R> &B, const Launch &L, co
         for (int q = 0; q < U; ++q) u[q] = fetch(q == 0 || k + q * TPA < nn ? e[q] : e[0]);
 #pragma unroll
         for (int q = 0; q < U; ++q) {
-            const PairIn<R> p = pair_vector<R>(ui, u[q], sh[e[q] >> kCodeShift]);
+            const PairIn<R> p = pair_vector<R>(ui, u[q], entry_shift<R>(e[q], h));
             if ((q == 0 || k + q * TPA < nn) && p.r2 < rc2) {
                 R rinv, r;
                 inv_r(p.r2, rinv, r);
@@ -408,8 +407,8 @@ __global__ void __launch_bounds__(256) k_density(Bufs<R> B, Geom G, Launch L)
 {
     using R4 = typename V4<R>::T;
     constexpr int U = PairsInFlight<MULTI>::U;
-    __shared__ R4 sh[27];
-    fill_shift<R>(sh, G);
+    R h[3];
+    load_h<R>(G, h);
     const DevState *st = B.st;
     const int sp = st->sp, s = st->set;
     R4 *sw = B.shadow[sp];
@@ -426,10 +425,10 @@ __global__ void __launch_bounds__(256) k_density(Bufs<R> B, Geom G, Launch L)
     if (active) {
         const int nn = B.nnb[i];
         if (tiled)
-            rho = density_lane<R, MULTI, TPA, U>(B, sh, rc2, s, nn, l, sw[i], ListTile{tile + (i - i0), width},
+            rho = density_lane<R, MULTI, TPA, U>(B, h, rc2, s, nn, l, sw[i], ListTile{tile + (i - i0), width},
                                                  GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2});
         else
-            rho = density_lane<R, MULTI, TPA, U>(B, sh, rc2, s, nn, l, sw[i], ListGlobal{B.list + i, L.ld},
+            rho = density_lane<R, MULTI, TPA, U>(B, h, rc2, s, nn, l, sw[i], ListGlobal{B.list + i, L.ld},
                                                  GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2});
     }
     rho = lane_sum<TPA>(rho);
@@ -446,8 +445,8 @@ __global__ void __launch_bounds__(256) k_force(Bufs<R> B, Geom G, Launch L)
 {
     using R4 = typename V4<R>::T;
     constexpr int U = PairsInFlight<MULTI>::U;
-    __shared__ R4 sh[27];
-    fill_shift<R>(sh, G);
+    R h[3];
+    load_h<R>(G, h);
     const DevState *st = B.st;
     const int sp = st->sp, s = st->set;
     const R4 *sw = B.shadow[sp];
@@ -465,10 +464,10 @@ __global__ void __launch_bounds__(256) k_force(Bufs<R> B, Geom G, Launch L)
     if (active) {
         const int nn = B.nnb[i];
         if (tiled)
-            force_lane<R, MULTI, ENERGY, TPA, U>(B, L, sh, rc2, s, nn, l, ti, sw[i], ListTile{tile + (i - i0), width},
+            force_lane<R, MULTI, ENERGY, TPA, U>(B, L, h, rc2, s, nn, l, ti, sw[i], ListTile{tile + (i - i0), width},
                                                  GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2});
         else
-            force_lane<R, MULTI, ENERGY, TPA, U>(B, L, sh, rc2, s, nn, l, ti, sw[i], ListGlobal{B.list + i, L.ld},
+            force_lane<R, MULTI, ENERGY, TPA, U>(B, L, h, rc2, s, nn, l, ti, sw[i], ListGlobal{B.list + i, L.ld},
                                                  GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2});
     }
 #pragma unroll
@@ -523,14 +522,14 @@ __global__ void __launch_bounds__(256) k_density_rows(Bufs<R> B, Geom G, Launch 
 {
     using R4 = typename V4<R>::T;
     R4 *stage = reinterpret_cast<R4 *>(dyn);
-    __shared__ R4 sh[27];
     __shared__ int base[9], rstart[9], rcount[9];
-    fill_shift<R>(sh, G);
+    R h[3];
+    load_h<R>(G, h);
     const DevState *st = B.st;
     const int sp = st->sp, s = st->set;
     R4 *sw = B.shadow[sp];
     const bool staged = stage_rows<R>(B, G, L, sw, stage, base, rstart, rcount, blockIdx.x);
-    const int a0 = rstart[4], a1 = a0 + rcount[4];  // this row: t = 4 is (dy, dz) = (0, 0)
+    const int a0 = rstart[4], a1 = a0 + rcount[4];  // this row: entry_row 4 is (dy, dz) = (0, 0)
     const R rc2 = g_rc2<R>(G);
     const int per = blockDim.x / TPA;
     const int l = threadIdx.x % TPA;
@@ -543,10 +542,10 @@ __global__ void __launch_bounds__(256) k_density_rows(Bufs<R> B, Geom G, Launch 
             const int nn = B.nnb[i];
             const ListGlobal list{B.list + i, L.ld};
             if (staged)
-                rho = density_lane<R, false, TPA, 4>(B, sh, rc2, s, nn, l, stage[i - base[4]], list,
+                rho = density_lane<R, false, TPA, 4>(B, h, rc2, s, nn, l, stage[i - base[4]], list,
                                                      StagedFetch<R>{stage, base}, TabGlobal<R>{B.coef2});
             else
-                rho = density_lane<R, false, TPA, 4>(B, sh, rc2, s, nn, l, sw[i], list, GlobalFetch<R>{sw},
+                rho = density_lane<R, false, TPA, 4>(B, h, rc2, s, nn, l, sw[i], list, GlobalFetch<R>{sw},
                                                      TabGlobal<R>{B.coef2});
         }
         rho = lane_sum<TPA>(rho);
@@ -563,9 +562,9 @@ __global__ void __launch_bounds__(256) k_force_rows(Bufs<R> B, Geom G, Launch L)
 {
     using R4 = typename V4<R>::T;
     R4 *stage = reinterpret_cast<R4 *>(dyn);
-    __shared__ R4 sh[27];
     __shared__ int base[9], rstart[9], rcount[9];
-    fill_shift<R>(sh, G);
+    R h[3];
+    load_h<R>(G, h);
     const DevState *st = B.st;
     const int sp = st->sp, s = st->set;
     const R4 *sw = B.shadow[sp];
@@ -585,10 +584,10 @@ __global__ void __launch_bounds__(256) k_force_rows(Bufs<R> B, Geom G, Launch L)
             const int nn = B.nnb[i];
             const ListGlobal list{B.list + i, L.ld};
             if (staged)
-                force_lane<R, false, ENERGY, TPA, 4>(B, L, sh, rc2, s, nn, l, 0, stage[i - base[4]], list,
+                force_lane<R, false, ENERGY, TPA, 4>(B, L, h, rc2, s, nn, l, 0, stage[i - base[4]], list,
                                                      StagedFetch<R>{stage, base}, f, e7, TabGlobal<R>{B.coef2});
             else
-                force_lane<R, false, ENERGY, TPA, 4>(B, L, sh, rc2, s, nn, l, 0, sw[i], list, GlobalFetch<R>{sw}, f,
+                force_lane<R, false, ENERGY, TPA, 4>(B, L, h, rc2, s, nn, l, 0, sw[i], list, GlobalFetch<R>{sw}, f,
                                                      e7, TabGlobal<R>{B.coef2});
         }
 #pragma unroll
@@ -619,10 +618,11 @@ template <bool ENERGY, int TPA>
 __global__ void __launch_bounds__(256) k_density_tab(Bufs<float> B, Geom G, Launch L)
 {
     float4 *f_rows = reinterpret_cast<float4 *>(dyn);
-    __shared__ float4 sh[27];
     const int nint = B.tables->fphi.nint;
     copy_rows(B.coef2, nint, f_rows, nullptr);
-    fill_shift<float>(sh, G);  // ends with a block barrier
+    __syncthreads();
+    float h[3];
+    load_h<float>(G, h);
     const DevState *st = B.st;
     const int sp = st->sp, s = st->set;
     float4 *sw = B.shadow[sp];
@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(256) k_density_tab(Bufs<float> B, Geom G, Laun
         const bool active = i < L.n;
         float rho = 0.f;
         if (active)
-            rho = density_lane<float, false, TPA, 2>(B, sh, rc2, s, B.nnb[i], l, sw[i], ListGlobal{B.list + i, L.ld},
+            rho = density_lane<float, false, TPA, 2>(B, h, rc2, s, B.nnb[i], l, sw[i], ListGlobal{B.list + i, L.ld},
                                                      GlobalFetch<float>{sw}, tab);
         rho = lane_sum<TPA>(rho);
         if (active && l == 0) e_embed += embed<float>(B, sw, i, 0, rho);
@@ -653,9 +653,10 @@ __global__ void __launch_bounds__(256) k_force_tab(Bufs<float> B, Geom G, Launch
     const int nint = B.tables->fphi.nint;
     float4 *f_rows = reinterpret_cast<float4 *>(dyn);
     float4 *phi_rows = f_rows + nint;
-    __shared__ float4 sh[27];
     copy_rows(B.coef2, nint, f_rows, phi_rows);
-    fill_shift<float>(sh, G);
+    __syncthreads();
+    float h[3];
+    load_h<float>(G, h);
     const DevState *st = B.st;
     const int sp = st->sp, s = st->set;
     const float4 *sw = B.shadow[sp];
@@ -671,7 +672,7 @@ __global__ void __launch_bounds__(256) k_force_tab(Bufs<float> B, Geom G, Launch
         const bool active = i < L.n;
         float f[3] = {0, 0, 0};
         if (active)
-            force_lane<float, false, ENERGY, TPA, 2>(B, L, sh, rc2, s, B.nnb[i], l, 0, sw[i],
+            force_lane<float, false, ENERGY, TPA, 2>(B, L, h, rc2, s, B.nnb[i], l, 0, sw[i],
                                                      ListGlobal{B.list + i, L.ld}, GlobalFetch<float>{sw}, f, e7, tab);
 #pragma unroll
         for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);

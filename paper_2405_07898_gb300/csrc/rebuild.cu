@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256) k_build_list(Bufs<R> B, Geom G, int n, in
                     int ex = cx + dx;
                     ex += (ex < 0) ? nx : ((ex >= nx) ? -nx : 0);
                     const int e = row + ex;
-                    const uint32_t code = (uint32_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)) << kCodeShift;
+                    const uint32_t code = list_entry(0u, dx, dy, dz);
                     const R ox = (R)dx * hx - up.x, oy = (R)dy * hy - up.y, oz = (R)dz * hz - up.z;
                     const int q1 = B.cell_start[e + 1];
                     for (int q = B.cell_start[e]; q < q1; ++q) {
