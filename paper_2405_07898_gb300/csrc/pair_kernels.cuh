@@ -394,7 +394,8 @@ __device__ __forceinline__ void prefetch_warp_streams(const Bufs<R> &B, const La
 
 // Pairs in flight per lane: the type-dependent path needs more registers a pair.
 template <bool MULTI> struct PairsInFlight {
-    static constexpr int U = MULTI ? 2 : 4;
+    static constexpr int density = MULTI ? 2 : 4;
+    static constexpr int force = 2;
 };
 
 extern __shared__ __align__(32) unsigned char dyn[];
@@ -406,7 +407,7 @@ template <class R, bool MULTI, bool ENERGY, int TPA, bool LS>
 __global__ void __launch_bounds__(256) k_density(Bufs<R> B, Geom G, Launch L)
 {
     using R4 = typename V4<R>::T;
-    constexpr int U = PairsInFlight<MULTI>::U;
+    constexpr int U = PairsInFlight<MULTI>::density;
     R h[3];
     load_h<R>(G, h);
     const DevState *st = B.st;
@@ -444,7 +445,7 @@ template <class R, bool MULTI, int MODE, bool ENERGY, int TPA, bool LS>
 __global__ void __launch_bounds__(256) k_force(Bufs<R> B, Geom G, Launch L)
 {
     using R4 = typename V4<R>::T;
-    constexpr int U = PairsInFlight<MULTI>::U;
+    constexpr int U = PairsInFlight<MULTI>::force;
     R h[3];
     load_h<R>(G, h);
     const DevState *st = B.st;
