@@ -74,12 +74,20 @@ class ClockSampler:
         try:
             self._proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self._proc = None
             return
         self._thread = threading.Thread(target=self._read, daemon=True)
         self._thread.start()
+        # the timed region starts once the sampler is live
+        t0 = time.time()
+        while not self.rows and time.time() - t0 < 3.0:
+            time.sleep(0.01)
+
+    def mark(self):
+        """Start of the timed region: later samples are the ones reported."""
+        self._mark = len(self.rows)
 
     def _read(self):
         for line in self._proc.stdout:
@@ -95,11 +103,12 @@ class ClockSampler:
             self._proc.kill()
         if self._thread:
             self._thread.join(timeout=2)
-        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        rows = self.rows[getattr(self, "_mark", 0):] or self.rows
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
-        for r in self.rows:
+        for r in rows:
             if len(r) >= 9:
                 for k, nm in enumerate(names):
                     if r[5 + k].lower() == "active":
@@ -158,6 +167,7 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     if args.profiler_range:
         torch.cuda.profiler.start()
+    clocks.mark()
     e0.record(stream)
     for _ in range(args.steps):
         bench_step()
@@ -296,6 +306,76 @@ def run_sweep(args):
     print(json.dumps({"workload": "bcc_sweep_1000K_mixed", "unit": "timesteps/s", "sweep": rows}), flush=True)
 
 
+def run_batch(args):
+    """Batched replicas: 512 independent periodic systems of uneven size (half
+    BCC, half FCC, 200-1,200 K) advanced --batch-steps steps in one persistent
+    launch per md_batch_step call; atom-steps/s = sum of atoms x steps over
+    the CUDA-event time on the batch's stream."""
+    import torch
+    from paper_2405_07898_gb300 import binding, inputs as I
+
+    torch.cuda.set_device(0)
+    reps = I.replica_batch(512)
+    b = binding.MDBatch(reps)
+    b.step(10, DT_FS)
+    b.energy()
+    info0 = b.info()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(b.stream)
+    b.step(args.batch_steps, DT_FS)
+    e1.record(b.stream)
+    b.energy()
+    ms = e0.elapsed_time(e1)
+    info = b.info()
+    b.close()
+    print(json.dumps({"workload": "replicas_512_bcc_fcc_mixed", "metric": "atom-steps/s",
+                      "value": info["atoms"] * args.batch_steps / (ms * 1e-3), "unit": "atom-steps/s",
+                      "replicas": info["replicas"], "atoms": info["atoms"], "steps": args.batch_steps,
+                      "ms": ms, "kernel_launches": info["kernel_launches"] - info0["kernel_launches"],
+                      "blocks": info["blocks"], "threads_per_block": info["threads_per_block"],
+                      "rebuilds": info["rebuilds"] - info0["rebuilds"]}), flush=True)
+
+
+def run_adjoint(args):
+    """Differentiation: force-matching loss over 64 BCC configurations of
+    2,000 atoms and its gradient over 3 x 64 spline knots (adjoint kernels,
+    FP64): seconds per loss+gradient evaluation, and the relative difference
+    of the gradient from central finite differences of the loss on a sample
+    of knots."""
+    import numpy as np
+    import torch
+    from paper_2405_07898_gb300 import autodiff, inputs as I
+
+    torch.cuda.set_device(0)
+    prob = I.fit_problem()
+    fm = autodiff.ForceMatch(prob)
+    theta = prob.theta0.copy()
+    fm.evaluate(theta, grad=True)
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        loss, g = fm.evaluate(theta, grad=True)
+    t_eval = (time.perf_counter() - t0) / reps
+    rng = np.random.default_rng(7898)
+    ks = rng.choice(len(theta), size=12, replace=False)
+    fd = []
+    for k in ks:
+        h = 1e-5 * max(abs(theta[k]), 1e-3)
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd.append((fm.evaluate(tp, grad=False)[0] - fm.evaluate(tm, grad=False)[0]) / (2 * h))
+    fd = np.array(fd)
+    err = float(np.linalg.norm(g[ks] - fd) / np.linalg.norm(fd))
+    fm.close()
+    print(json.dumps({"workload": "force_match_64x2000_bcc", "metric": "s per loss+gradient",
+                      "value": t_eval, "unit": "s", "higher_is_better": False, "configs": len(prob.configs),
+                      "knots": int(len(theta)), "loss": float(loss),
+                      "gradient_vs_central_fd_rel_err_12_knots": err}), flush=True)
+
+
 def run_drift(args):
     """NVE energy drift: the 250,000-atom Sigma-5 bicrystal at 1,000 K and the
     799,496-atom box at 300 K, mixed precision, dt = 2 fs; total energy
@@ -418,7 +498,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -426,10 +506,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="bcc_799496", choices=["bcc_799496", "sweep", "drift"],
+    ap.add_argument("--workload", default="bcc_799496", choices=["bcc_799496", "sweep", "drift", "batch", "adjoint"],
                     help="bcc_799496: the benchmark line; sweep / drift: the strong-scaling sweep and the "
                          "NVE drift runs (their own JSON lines)")
     ap.add_argument("--drift-steps", type=int, default=100000)
+    ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--cells", type=int, nargs=3, default=None,
                     help="BCC cells per axis of a smaller profiling case (default: the 74x74x73 workload)")
     ap.add_argument("--profiler-range", action="store_true",
@@ -446,6 +527,10 @@ def main():
         run_sweep(args)
     elif args.workload == "drift":
         run_drift(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 
