@@ -273,35 +273,32 @@ def _timed_steps(md, nsteps, dt, reps=1):
 
 def run_sweep(args):
     """Strong-scaling sweep: BCC cubes of 1,024 .. 314,928 atoms and the
-    799,496-atom box at 1,000 K (mixed precision): timesteps/s of the graph
-    path, and for systems that fit one thread block's schedule (<= 20,000
-    atoms) of the persistent single-replica path."""
+    799,496-atom box at 1,000 K (mixed precision): timesteps/s of md_step
+    replayed as CUDA graphs and, up to 314,928 atoms, as one cooperative
+    launch per call (the path the library picks automatically up to 65,536
+    atoms)."""
     import torch
     from paper_2405_07898_gb300 import binding, inputs as I
 
     torch.cuda.set_device(0)
     rows = []
     for s in I.sweep_systems(temperature=1000.0):
-        md = binding.MD(s, precision="mixed")
         steps = max(200, min(20000, int(2e8 // s.n) // 10 * 10))
-        md.step(100, DT_FS)
-        t = _timed_steps(md, steps, DT_FS)
-        row = {"atoms": s.n, "steps": steps, "graph_ts_per_s": steps / t,
-               "graph_atom_steps_per_s": s.n * steps / t}
-        md.close()
-        if s.n <= 20000:
-            b = binding.MDBatch([s])
-            b.step(100, DT_FS)
-            b.energy()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(b.stream)
-            b.step(steps, DT_FS)
-            e1.record(b.stream)
-            b.energy()
-            tb = e0.elapsed_time(e1) * 1e-3
-            row["persistent_ts_per_s"] = steps / tb
-            b.close()
+        row = {"atoms": s.n, "steps": steps}
+        for mode in ("off", "on"):
+            if mode == "on" and s.n > 400000:
+                continue
+            md = binding.MD(s, precision="mixed", persistent=mode)
+            md.step(100, DT_FS)
+            t = _timed_steps(md, steps, DT_FS)
+            key = "graph" if mode == "off" else "single_launch"
+            row[key + "_ts_per_s"] = steps / t
+            row[key + "_atom_steps_per_s"] = s.n * steps / t
+            if mode == "on":
+                st = md.stats()
+                row["single_launch_blocks"] = st["persistent_blocks"]
+                row["single_launch_lanes"] = st["persistent_lanes"]
+            md.close()
         rows.append(row)
     print(json.dumps({"workload": "bcc_sweep_1000K_mixed", "unit": "timesteps/s", "sweep": rows}), flush=True)
 

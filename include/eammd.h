@@ -82,6 +82,7 @@ typedef struct {
 } md_potential;
 
 enum { MD_PRECISION_FP64 = 0, MD_PRECISION_MIXED = 1 };
+enum { MD_PERSIST_AUTO = 0, MD_PERSIST_OFF = 1, MD_PERSIST_ON = 2 };
 enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2, MD_SCHEDULE_TILES = 3,
        MD_SCHEDULE_TABLE = 4 };
 
@@ -137,6 +138,18 @@ enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2, MD_SCH
  *                    memory and walk tiles of atoms; lanes_per_atom 1, 2 or
  *                    4; forces bitwise those of MD_SCHEDULE_ATOMS.  Falls
  *                    back to MD_SCHEDULE_ATOMS where it does not apply.
+ *   persistent       MD_PERSIST_AUTO (0): md_step runs as one cooperative
+ *                    launch (all phases of all steps, blocks meeting at grid
+ *                    barriers) for systems of at most 20,000 atoms, else as
+ *                    CUDA graphs.  MD_PERSIST_OFF: always the graph (or
+ *                    eager) path.  MD_PERSIST_ON: always the single launch.
+ *                    Lanes per atom of the single launch: lanes_per_atom, or
+ *                    timed at md_create over 1, 2, 4, 8 on steps at dt = 0
+ *                    (the state is restored).  Positions, velocities and
+ *                    forces are bitwise those of the graph path with the same
+ *                    lanes per atom; energy sums differ in rounding only.  A
+ *                    grid-barrier wait longer than 1 s ends the launch and
+ *                    raises MD_ERR_TIMEOUT.
  *   stage_capacity   records a row-staged block holds; 0 = 1.1 x the most
  *                    that any 3 x 3 block of rows holds at md_create, + 32.
  *                    Must fit the shared memory of a block (160 KB of
@@ -154,6 +167,7 @@ typedef struct {
     void *alloc_ctx;
     int32_t schedule;
     int32_t stage_capacity;
+    int32_t persistent;
 } md_options;
 
 void md_options_default(md_options *opt);
@@ -227,6 +241,8 @@ typedef struct {
     int32_t table_force;     /* 1: force pass likewise */
     int32_t threads_density; /* threads per block of the density pass */
     int32_t threads_force;   /* threads per block of the force pass */
+    int32_t persistent_blocks; /* blocks of the single-launch md_step (0: graphs) */
+    int32_t persistent_lanes;  /* lanes per atom of its pair passes */
 } md_stats_t;
 
 md_status md_stats(md_ctx *ctx, md_stats_t *out);

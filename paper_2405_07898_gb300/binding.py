@@ -24,6 +24,7 @@ STATUS = {0: "MD_OK", -1: "MD_ERR_ARG", -2: "MD_ERR_BOX", -3: "MD_ERR_CUDA", -4:
           -5: "MD_ERR_NONFINITE", -6: "MD_ERR_TIMEOUT", -7: "MD_ERR_LIST_OVERFLOW",
           -8: "MD_ERR_CAPACITY"}
 PRECISION = {"fp64": 0, "mixed": 1}
+PERSIST = {"auto": 0, "off": 1, "on": 2}
 SCHEDULE = {"auto": 0, "atoms": 1, "rows": 2, "tiles": 3, "table": 4}
 
 # every entry point declared in include/eammd.h
@@ -55,7 +56,8 @@ class Options(C.Structure):
                 ("block_size", C.c_int32), ("lanes_per_atom", C.c_int32),
                 ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("schedule", C.c_int32),
-                ("stage_capacity", C.c_int32)]
+                ("stage_capacity", C.c_int32),
+                ("persistent", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -66,7 +68,8 @@ class Stats(C.Structure):
                 ("rows_force", C.c_int32), ("stage_capacity", C.c_int32), ("tiles_density", C.c_int32),
                 ("tiles_force", C.c_int32), ("table_density", C.c_int32),
                 ("table_force", C.c_int32), ("threads_density", C.c_int32),
-                ("threads_force", C.c_int32)]
+                ("threads_force", C.c_int32), ("persistent_blocks", C.c_int32),
+                ("persistent_lanes", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -220,7 +223,7 @@ class MD:
     def __init__(self, system, precision: str = "mixed", rebuild_every: int = 10,
                  list_capacity: int = 0, use_graphs: bool = True, block_size: int = 256,
                  lanes_per_atom: int = 0, use_torch: bool | None = None, schedule: str = "auto",
-                 stage_capacity: int = 0):
+                 stage_capacity: int = 0, persistent: str = "auto"):
         L = load()
         self._L = L
         self.n = int(system.n)
@@ -235,6 +238,7 @@ class MD:
         opt.lanes_per_atom = lanes_per_atom
         opt.schedule = SCHEDULE[schedule]
         opt.stage_capacity = stage_capacity
+        opt.persistent = PERSIST[persistent]
         self._keep = []
         if use_torch is None:
             try:

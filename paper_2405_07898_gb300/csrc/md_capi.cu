@@ -97,6 +97,9 @@ struct md_ctx {
     int *adj_knot_func = nullptr, *adj_func_coef0 = nullptr, *adj_func_ncoef = nullptr;
     long long *adj_knot_mt0 = nullptr;
     int adj_nrows = 0, adj_nknots = 0;
+    // persistent step launch (md_step as one cooperative kernel)
+    PersistScratch *ps = nullptr;
+    int persist_tpa = 0, persist_grid = 0;  // 0: graph path
     std::string err;
 
     md_status fail(md_status s, const std::string &m)
@@ -426,6 +429,11 @@ md_status step_impl(md_ctx *ctx, int64_t nsteps, double dt)
     Launch L = ctx->L;
     L.use_cond = 0;
     L.cond = 0;
+    if (ctx->persist_grid > 0) {
+        CK(launch_steps<R>(B, ctx->G, L, nsteps, ctx->persist_tpa, ctx->persist_grid, ctx->ps));
+        ctx->fixed_launches += 1;
+        return MD_OK;
+    }
     ctx->fixed_launches += launch_open<R>(B, ctx->G, L);
     if (!ctx->opt.use_graphs) {
         for (int64_t s = 0; s < nsteps; ++s) {
@@ -773,6 +781,89 @@ md_status autotune(md_ctx *ctx)
     return check_device_errors(ctx);
 }
 
+// Threshold of MD_PERSIST_AUTO: at and below this many atoms a step is a few
+// microseconds of work and one cooperative launch per md_step call beats the
+// graph replay (measured on GB300 over the BCC sweep).
+constexpr int64_t kPersistentAutoAtoms = 20000;
+
+// The persistent step launch: lanes per atom (from the options, else timed
+// over 1, 2, 4, 8 on rebuild_every - 1 steps at dt = 0, which moves no atom
+// and builds no list; the device state is restored after each trial) and the
+// resident grid.
+template <class R>
+md_status setup_persistent(md_ctx *ctx)
+{
+    ctx->persist_grid = 0;
+    const md_options &o = ctx->opt;
+    const bool want = o.persistent == MD_PERSIST_ON || (o.persistent == MD_PERSIST_AUTO && ctx->n <= kPersistentAutoAtoms);
+    if (!want || ctx->n == 0) return MD_OK;
+    if (!ctx->ps) {
+        if (!alloc_n(ctx, ctx->ps, 1)) return ctx->fail(MD_ERR_OOM, "device allocation failed");
+        CK(cudaMemsetAsync(ctx->ps, 0, sizeof(PersistScratch), ctx->stream));
+    }
+    int dev = 0, coop = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) {
+        if (o.persistent == MD_PERSIST_ON) return ctx->fail(MD_ERR_CUDA, "the device has no cooperative launch");
+        return MD_OK;
+    }
+    const Bufs<R> &B = bufs<R>(ctx);
+    std::vector<int> cand;
+    if (o.lanes_per_atom > 0) cand.push_back(o.lanes_per_atom);
+    else if (ctx->L.rebuild_every < 2) cand.push_back(2);  // every step builds: no state-neutral trial
+    else cand = {1, 2, 4, 8};
+    if (cand.size() == 1) {
+        ctx->persist_tpa = cand[0];
+        ctx->persist_grid = persistent_grid<R>(ctx->L, cand[0]);
+        if (ctx->persist_grid <= 0 && o.persistent == MD_PERSIST_ON)
+            return ctx->fail(MD_ERR_CUDA, "the persistent step kernel cannot be resident");
+        return MD_OK;
+    }
+    const int trial_steps = ctx->L.rebuild_every - 1;
+    DevState saved;
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(&saved, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    Launch L = ctx->L;
+    L.dt = 0.0;
+    for (int t = 0; t < ctx->ntypes; ++t) L.half_kick[t] = 0.0;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_tpa = 0, best_grid = 0;
+    for (int round = 0; round < (cand.size() > 1 ? 3 : 1); ++round) {
+        for (int tpa : cand) {
+            const int grid = persistent_grid<R>(ctx->L, tpa);
+            if (grid <= 0) continue;
+            CK(cudaEventRecord(e0, ctx->stream));
+            CK(launch_steps<R>(B, ctx->G, L, trial_steps, tpa, grid, ctx->ps));
+            CK(cudaEventRecord(e1, ctx->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            CK(cudaMemcpy(ctx->st, &saved, sizeof(DevState), cudaMemcpyHostToDevice));
+            ctx->fixed_launches += 1;
+            // a wider schedule must win by 3%
+            if (ms < 0.97f * best) {
+                best = ms;
+                best_tpa = tpa;
+                best_grid = grid;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (saved.error) return check_device_errors(ctx);
+    if (best_grid <= 0) {
+        if (o.persistent == MD_PERSIST_ON) return ctx->fail(MD_ERR_CUDA, "the persistent step kernel cannot be resident");
+        return MD_OK;
+    }
+    ctx->persist_tpa = best_tpa;
+    ctx->persist_grid = best_grid;
+    return check_device_errors(ctx);
+}
+
 // Replace the spline values of a context (same grids, same r_cut and skin)
 // and re-evaluate forces and energies at the current positions.
 template <class R>
@@ -958,10 +1049,15 @@ md_status create_impl(md_ctx *ctx, const double *pos, const double *vel, const i
         set_sched(ctx, p, p);
         rc = reevaluate<R>(ctx);
         if (rc != MD_OK) return rc;
-        return check_device_errors(ctx);
+        rc = check_device_errors(ctx);
+        if (rc != MD_OK) return rc;
+        return setup_persistent<R>(ctx);
     }
-    if (o.lanes_per_atom == 0 && o.schedule == MD_SCHEDULE_AUTO) return autotune<R>(ctx);
-    return MD_OK;
+    if (o.lanes_per_atom == 0 && o.schedule == MD_SCHEDULE_AUTO) {
+        rc = autotune<R>(ctx);
+        if (rc != MD_OK) return rc;
+    }
+    return setup_persistent<R>(ctx);
 }
 
 }  // namespace
@@ -1039,6 +1135,8 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     if (o.schedule >= MD_SCHEDULE_ROWS && o.lanes_per_atom == 8)
         return bad(MD_ERR_ARG, "row-staged, list-tiled and shared-table passes take 1, 2 or 4 lanes per atom");
     if (o.stage_capacity < 0) return bad(MD_ERR_ARG, "stage_capacity must be >= 0");
+    if (o.persistent < MD_PERSIST_AUTO || o.persistent > MD_PERSIST_ON)
+        return bad(MD_ERR_ARG, "persistent must be MD_PERSIST_AUTO, _OFF or _ON");
 
     md_ctx *ctx = new (std::nothrow) md_ctx();
     if (!ctx) return bad(MD_ERR_OOM, "host allocation failed");
@@ -1285,6 +1383,8 @@ md_status md_stats(md_ctx *ctx, md_stats_t *out)
     out->table_force = ctx->L.tab_f;
     out->threads_density = ctx->L.block_d;
     out->threads_force = ctx->L.block_f;
+    out->persistent_blocks = ctx->persist_grid;
+    out->persistent_lanes = ctx->persist_tpa;
     out->stage_capacity = ctx->L.stage_cap;
     return MD_OK;
 }

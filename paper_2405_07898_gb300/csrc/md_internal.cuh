@@ -171,13 +171,29 @@ struct Launch {
 
 enum StepMode { MODE_MEASURE = 0, MODE_CLOSE = 1, MODE_CLOSE_OPEN = 2 };
 
-// Host-side launchers (rebuild.cu, pair_f32.cu, pair_f64.cu).  All are asynchronous on L.stream and
+// Device words of the persistent step kernel: grid-barrier arrival counter
+// and generation, and the two alternating largest-displacement words.
+struct PersistScratch {
+    unsigned count, gen;
+    unsigned maxdisp[2];
+};
+constexpr int kPersistentBlock = 256;
+
+// Host-side launchers (rebuild.cu, pair_f32.cu, pair_f64.cu, persistent.cu).  All are asynchronous on L.stream and
 // return the number of kernels queued.
 template <class R> int launch_rebuild(const Bufs<R> &B, const Geom &G, const Launch &L);
 template <class R> int launch_decide(const Bufs<R> &B, const Launch &L);
 template <class R> int launch_open(const Bufs<R> &B, const Geom &G, const Launch &L);
 template <class R> int launch_density(const Bufs<R> &B, const Geom &G, const Launch &L, bool energy);
 template <class R> int launch_force(const Bufs<R> &B, const Geom &G, const Launch &L, int mode, bool energy);
+// md_step as one cooperative launch of `grid` blocks with `tpa` lanes per atom
+// in the pair passes (persistent.cu); persistent_grid: the blocks that can be
+// resident at once for that kernel (0 if it cannot be launched).
+template <class R> int persistent_grid(const Launch &L, int tpa);
+template <class R>
+cudaError_t launch_steps(const Bufs<R> &B, const Geom &G, const Launch &L, long long nsteps, int tpa, int grid,
+                         PersistScratch *ps);
+
 // Opt the row-staged and list-tiled passes in to `bytes` of dynamic shared
 // memory.
 template <class R> cudaError_t allow_shared_staging(int bytes);

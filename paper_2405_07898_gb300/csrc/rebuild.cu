@@ -11,7 +11,7 @@
 // R is the pair-arithmetic type: float in the mixed-precision path, double in
 // the FP64 path.  Positions, velocities, the drift and all sums over atoms are
 // FP64 in both paths.
-#include "device_common.cuh"
+#include "rebuild_device.cuh"
 
 #include <cuda_runtime.h>
 
@@ -21,41 +21,13 @@ namespace {
 // --------------------------------------------------------------------------
 // list build (every rebuild): wrap, bin, scan, scatter, sort, permute, list
 
-// Wrap x = xr + d into [0, L) exactly as x - L floor(x / L) (for |x| < 2L the
-// branch form below gives the same bits), then bin: c_d = floor(x_d n_d/L_d).
 template <class R>
 __global__ void k_bin(Bufs<R> B, Geom G, int n)
 {
     const DevState *st = B.st;
     if (!st->need_rebuild) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int s = st->set;
-    int c[3];
-    bool finite = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double L = G.box[a];
-        double x = __dadd_rn(B.xr[s][a][i], B.d[a][i]);
-        if (x >= 0.0 && x < L) {
-        } else if (x < 0.0 && x >= -L) {
-            x = __dadd_rn(x, L);
-        } else if (x >= L && x < 2.0 * L) {
-            x = __dsub_rn(x, L);
-        } else {
-            double q = floor(__ddiv_rn(x, L));
-            x = __dsub_rn(x, __dmul_rn(L, q));
-        }
-        finite = finite && isfinite(x);
-        B.xw[a][i] = x;
-        double q = floor(__dmul_rn(x, G.inv_cell[a]));
-        int ca = finite ? (int)fmax(fmin(q, (double)(G.ncell[a] - 1)), 0.0) : 0;
-        c[a] = ca;
-    }
-    if (!finite) atomicOr(&B.st->error, ERR_NONFINITE);
-    int cell = (c[2] * G.ncell[1] + c[1]) * G.ncell[0] + c[0];
-    B.cell_old[i] = cell;
-    B.slot[i] = atomicAdd(&B.count[cell], 1);
+    if (i < n) bin_atom<R>(B, G, st->set, i);
 }
 
 // Per block of kScanBlock cells: total count.
@@ -125,60 +97,24 @@ __global__ void k_scatter(Bufs<R> B, int n)
 {
     if (!B.st->need_rebuild) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    B.cell_atoms[B.cell_start[B.cell_old[i]] + B.slot[i]] = i;
+    if (i < n) scatter_atom<R>(B, i);
 }
 
-// Within each cell, order atoms by original id (the atomics above leave
-// them in arrival order); insertion sort, cells hold a handful of atoms.
 template <class R>
 __global__ void k_cell_sort(Bufs<R> B, int ncells)
 {
     if (!B.st->need_rebuild) return;
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncells) return;
-    const int *id = B.id[B.st->set];
-    int s = B.cell_start[c], e = B.cell_start[c + 1];
-    for (int q = s + 1; q < e; ++q) {
-        int a = B.cell_atoms[q];
-        int ka = id[a];
-        int r = q - 1;
-        while (r >= s && id[B.cell_atoms[r]] > ka) {
-            B.cell_atoms[r + 1] = B.cell_atoms[r];
-            --r;
-        }
-        B.cell_atoms[r + 1] = a;
-    }
+    if (c < ncells) sort_cell<R>(B, B.st->set, c);
 }
 
-// Gather the state into cell order (the other buffer set): positions become
-// the wrapped positions, displacements restart at zero, and the cell-centred
-// coordinates uref (and this step's shadow) are formed in FP64 and rounded.
 template <class R>
 __global__ void k_permute(Bufs<R> B, Geom G, int n)
 {
     const DevState *st = B.st;
     if (!st->need_rebuild) return;
     int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const int s = st->set, t = 1 - s, sp = st->sp;
-    int i = B.cell_atoms[p];
-    int cell = B.cell_old[i];
-    int cc[3] = {cell % G.ncell[0], (cell / G.ncell[0]) % G.ncell[1], cell / (G.ncell[0] * G.ncell[1])};
-    R u[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double X = B.xw[a][i];
-        B.xr[t][a][p] = X;
-        u[a] = (R)__dsub_rn(X, B.center[a][cc[a]]);
-        B.uref[a][p] = u[a];
-        B.v[t][a][p] = B.v[s][a][i];
-        B.d[a][p] = 0.0;
-    }
-    B.shadow[sp][p] = mk4<R>(u[0], u[1], u[2], (R)0);
-    B.id[t][p] = B.id[s][i];
-    B.type[t][p] = B.type[s][i];
-    B.cell[p] = cell;
+    if (p < n) permute_atom<R>(B, G, st->set, st->sp, p);
 }
 
 template <class R>
@@ -193,91 +129,14 @@ __global__ void k_rebuild_finish(Bufs<R> B, int in_graph)
     st->max_nnb = 0;
 }
 
-// Exact list test for a candidate near the list radius: the minimum-image
-// squared distance with the operations and rounding order of the definition
-// (d = x_j - x_i, +-L once, (dx^2 + dy^2) + dz^2, no fused operations).
-__device__ __forceinline__ bool exact_in_list(const double *const xr[3], int p, int q, const Geom &G)
-{
-    double d[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double x = __dsub_rn(xr[a][q], xr[a][p]);
-        if (x > G.half_box[a]) x = __dsub_rn(x, G.box[a]);
-        else if (x < -G.half_box[a]) x = __dadd_rn(x, G.box[a]);
-        d[a] = x;
-    }
-    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
-    return r2 < G.rl2;
-}
-
-// Verlet list: for each atom the atoms of the 27 surrounding cells (in
-// stencil order, ascending id inside a cell) closer than r_list.  The test
-// runs in R on the cell-centred coordinates; candidates within the rounding
-// margin of r_list are decided by exact_in_list, so the list is bit-identical
-// to the FP64 definition.  The stencil loop is unrolled: cell codes and
-// shifts are constants of each unrolled iteration.
 template <class R>
 __global__ void __launch_bounds__(256) k_build_list(Bufs<R> B, Geom G, int n, int ld, int cap)
 {
-    using R4 = typename V4<R>::T;
     DevState *st = B.st;
     if (!st->need_rebuild) return;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    int cnt = 0;
-    if (p < n) {
-        const int sp = st->sp, s = st->set;
-        const double *const xr[3] = {B.xr[s][0], B.xr[s][1], B.xr[s][2]};
-        const R4 *sw = B.shadow[sp];
-        const R lo = g_screen_lo<R>(G), hi = g_screen_hi<R>(G);
-        const R hx = g_h<R>(G, 0), hy = g_h<R>(G, 1), hz = g_h<R>(G, 2);
-        const int nx = G.ncell[0], ny = G.ncell[1], nz = G.ncell[2];
-        const int cell = B.cell[p];
-        const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
-        const R4 up = sw[p];
-        uint32_t *lp = B.list + p;
-#pragma unroll
-        for (int dz = -1; dz <= 1; ++dz) {
-            int ez = cz + dz;
-            ez += (ez < 0) ? nz : ((ez >= nz) ? -nz : 0);
-#pragma unroll
-            for (int dy = -1; dy <= 1; ++dy) {
-                int ey = cy + dy;
-                ey += (ey < 0) ? ny : ((ey >= ny) ? -ny : 0);
-                const int row = (ez * ny + ey) * nx;
-#pragma unroll
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int ex = cx + dx;
-                    ex += (ex < 0) ? nx : ((ex >= nx) ? -nx : 0);
-                    const int e = row + ex;
-                    const uint32_t code = list_entry(0u, dx, dy, dz);
-                    const R ox = (R)dx * hx - up.x, oy = (R)dy * hy - up.y, oz = (R)dz * hz - up.z;
-                    const int q1 = B.cell_start[e + 1];
-                    for (int q = B.cell_start[e]; q < q1; ++q) {
-                        const R4 uq = sw[q];
-                        const R ddx = uq.x + ox, ddy = uq.y + oy, ddz = uq.z + oz;
-                        const R r2 = fma(ddz, ddz, fma(ddy, ddy, ddx * ddx));
-                        if (r2 > hi || q == p) continue;
-                        if (r2 < lo || exact_in_list(xr, p, q, G)) {
-                            if (cnt < cap) lp[(size_t)cnt * ld] = (uint32_t)q | code;
-                            ++cnt;
-                        }
-                    }
-                }
-            }
-        }
-        B.nnb[p] = min(cnt, cap);
-        if (cnt > cap) atomicOr(&st->error, ERR_LIST_OVERFLOW);
-    }
-    // block maximum of the neighbour counts, one atomic per block
-    __shared__ int smax[32];
-    int m = cnt;
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)((blockDim.x + 31) >> 5); ++w) m = max(m, smax[w]);
-        if (m > *(volatile int *)&st->max_nnb) atomicMax(&st->max_nnb, m);
-    }
+    const int cnt = (p < n) ? list_atom<R>(B, G, st->set, st->sp, p, ld, cap) : 0;
+    block_max_nnb(cnt, &st->max_nnb);
 }
 
 // --------------------------------------------------------------------------
@@ -304,28 +163,9 @@ __global__ void k_decide(DevState *st, int rebuild_every, double disp2_thr, cuda
 template <class R>
 __global__ void k_open(Bufs<R> B, Launch L)
 {
-    using R4 = typename V4<R>::T;
     const DevState *st = B.st;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = st->set, sp = st->sp;
-    float d2 = 0.f;
-    if (i < L.n) {
-        int ti = L.ntypes > 1 ? B.type[s][i] : 0;
-        double kq = L.half_kick[ti];
-        double dn[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            double v = B.v[s][a][i];
-            v = fma((double)B.fcache[a][i], kq, v);
-            B.v[s][a][i] = v;
-            dn[a] = fma(v, L.dt, B.d[a][i]);
-            B.d[a][i] = dn[a];
-        }
-        R u0 = B.uref[0][i] + (R)dn[0], u1 = B.uref[1][i] + (R)dn[1], u2 = B.uref[2][i] + (R)dn[2];
-        B.shadow[sp ^ 1][i] = mk4<R>(u0, u1, u2, (R)0);
-        float fx = (float)dn[0], fy = (float)dn[1], fz = (float)dn[2];
-        d2 = fx * fx + fy * fy + fz * fz;
-    }
+    const float d2 = (i < L.n) ? open_atom<R>(B, L, st->set, st->sp, i) : 0.f;
     block_max_disp(d2, &B.st->maxdisp2);
 }
 
@@ -335,23 +175,8 @@ __global__ void k_open(Bufs<R> B, Launch L)
 template <class R>
 __global__ void __launch_bounds__(1024) k_reduce(Bufs<R> B, int nb_d, int nb_f, int stride)
 {
-    __shared__ double sm[32];
     const int slot = blockIdx.x;
-    const int nb = slot == 0 ? nb_d : nb_f;
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += B.partials[(size_t)slot * stride + b];
-    s = warp_sum_d(s);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[w];
-        DevState *st = B.st;
-        if (slot == 0) st->e_embed = t;
-        else if (slot == 1) st->e_pair = t;
-        else if (slot == 2) st->ke = t;
-        else st->virial[slot - 3] = t;
-    }
+    reduce_slot(B.partials, B.st, slot, slot == 0 ? nb_d : nb_f, stride);
 }
 
 // Host arrays in, device SoA out: state of md_create / md_set_state in the

@@ -1,0 +1,273 @@
+// rebuild_device.cuh -- per-element device functions of the list rebuild,
+// the opening kick and the energy reduction.  The kernels of rebuild.cu launch
+// them one element per thread; the persistent step kernel (persistent.cu)
+// runs them in grid-stride loops between grid barriers.  Every function takes
+// the buffer set `s` and the record buffer `sp` explicitly.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace eammd {
+namespace {
+
+// Wrap x = xr + d into [0, L) exactly as x - L floor(x / L) (for |x| < 2L the
+// branch form below gives the same bits), then bin: c_d = floor(x_d n_d/L_d).
+// The slot inside the cell is the arrival order (fixed by sort_cell).
+template <class R>
+__device__ __forceinline__ void bin_atom(const Bufs<R> &B, const Geom &G, int s, int i)
+{
+    int c[3];
+    bool finite = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double L = G.box[a];
+        double x = __dadd_rn(B.xr[s][a][i], B.d[a][i]);
+        if (x >= 0.0 && x < L) {
+        } else if (x < 0.0 && x >= -L) {
+            x = __dadd_rn(x, L);
+        } else if (x >= L && x < 2.0 * L) {
+            x = __dsub_rn(x, L);
+        } else {
+            double q = floor(__ddiv_rn(x, L));
+            x = __dsub_rn(x, __dmul_rn(L, q));
+        }
+        finite = finite && isfinite(x);
+        B.xw[a][i] = x;
+        double q = floor(__dmul_rn(x, G.inv_cell[a]));
+        int ca = finite ? (int)fmax(fmin(q, (double)(G.ncell[a] - 1)), 0.0) : 0;
+        c[a] = ca;
+    }
+    if (!finite) atomicOr(&B.st->error, ERR_NONFINITE);
+    int cell = (c[2] * G.ncell[1] + c[1]) * G.ncell[0] + c[0];
+    B.cell_old[i] = cell;
+    B.slot[i] = atomicAdd(&B.count[cell], 1);
+}
+
+// Exclusive scan of all cell counts by one block (any size): cell_start[c] =
+// sum_{c' < c} count[c'], counts zeroed for the next build.  Each thread
+// scans a contiguous chunk; the chunk totals are scanned across the block.
+template <class R>
+__device__ __forceinline__ void scan_cells_block(const Bufs<R> &B, int ncells)
+{
+    __shared__ int tot[1024];
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int per = (ncells + nt - 1) / nt;
+    const int c0 = min(t * per, ncells), c1 = min(c0 + per, ncells);
+    int sum = 0;
+    for (int c = c0; c < c1; ++c) sum += B.count[c];
+    tot[t] = sum;
+    __syncthreads();
+    if (t == 0) {
+        int run = 0;
+        for (int k = 0; k < nt; ++k) {
+            const int v = tot[k];
+            tot[k] = run;
+            run += v;
+        }
+        B.cell_start[ncells] = run;
+    }
+    __syncthreads();
+    int run = tot[t];
+    for (int c = c0; c < c1; ++c) {
+        const int v = B.count[c];
+        B.cell_start[c] = run;
+        B.count[c] = 0;
+        run += v;
+    }
+    __syncthreads();
+}
+
+template <class R>
+__device__ __forceinline__ void scatter_atom(const Bufs<R> &B, int i)
+{
+    B.cell_atoms[B.cell_start[B.cell_old[i]] + B.slot[i]] = i;
+}
+
+// Within cell c, order atoms by original id (the atomics of bin_atom leave
+// them in arrival order); insertion sort, cells hold a handful of atoms.
+template <class R>
+__device__ __forceinline__ void sort_cell(const Bufs<R> &B, int s, int c)
+{
+    const int *id = B.id[s];
+    int lo = B.cell_start[c], hi = B.cell_start[c + 1];
+    for (int q = lo + 1; q < hi; ++q) {
+        int a = B.cell_atoms[q];
+        int ka = id[a];
+        int r = q - 1;
+        while (r >= lo && id[B.cell_atoms[r]] > ka) {
+            B.cell_atoms[r + 1] = B.cell_atoms[r];
+            --r;
+        }
+        B.cell_atoms[r + 1] = a;
+    }
+}
+
+// Gather the state of atom p (cell order) into the other buffer set:
+// positions become the wrapped positions, displacements restart at zero, and
+// the cell-centred coordinates uref (and record buffer sp) are formed in FP64
+// and rounded.
+template <class R>
+__device__ __forceinline__ void permute_atom(const Bufs<R> &B, const Geom &G, int s, int sp, int p)
+{
+    const int t = 1 - s;
+    int i = B.cell_atoms[p];
+    int cell = B.cell_old[i];
+    int cc[3] = {cell % G.ncell[0], (cell / G.ncell[0]) % G.ncell[1], cell / (G.ncell[0] * G.ncell[1])};
+    R u[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double X = B.xw[a][i];
+        B.xr[t][a][p] = X;
+        u[a] = (R)__dsub_rn(X, B.center[a][cc[a]]);
+        B.uref[a][p] = u[a];
+        B.v[t][a][p] = B.v[s][a][i];
+        B.d[a][p] = 0.0;
+    }
+    B.shadow[sp][p] = mk4<R>(u[0], u[1], u[2], (R)0);
+    B.id[t][p] = B.id[s][i];
+    B.type[t][p] = B.type[s][i];
+    B.cell[p] = cell;
+}
+
+// Exact list test for a candidate near the list radius: the minimum-image
+// squared distance with the operations and rounding order of the definition
+// (d = x_j - x_i, +-L once, (dx^2 + dy^2) + dz^2, no fused operations).
+__device__ __forceinline__ bool exact_in_list(const double *const xr[3], int p, int q, const Geom &G)
+{
+    double d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double x = __dsub_rn(xr[a][q], xr[a][p]);
+        if (x > G.half_box[a]) x = __dsub_rn(x, G.box[a]);
+        else if (x < -G.half_box[a]) x = __dadd_rn(x, G.box[a]);
+        d[a] = x;
+    }
+    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+    return r2 < G.rl2;
+}
+
+// Verlet list: for each atom the atoms of the 27 surrounding cells (in
+// stencil order, ascending id inside a cell) closer than r_list.  The test
+// runs in R on the cell-centred coordinates; candidates within the rounding
+// margin of r_list are decided by exact_in_list, so the list is bit-identical
+// to the FP64 definition.  The stencil loop is unrolled: cell codes and
+// shifts are constants of each unrolled iteration.
+// Verlet list of atom p: the atoms of the 27 surrounding cells (in stencil
+// order, ascending id inside a cell) closer than r_list.  The test runs in R
+// on the cell-centred coordinates; candidates within the rounding margin of
+// r_list are decided by exact_in_list, so the list is bit-identical to the
+// FP64 definition.  The stencil loop is unrolled: cell offsets and shifts are
+// constants of each unrolled iteration.  Returns the neighbour count (the
+// list keeps at most cap of them; more raises ERR_LIST_OVERFLOW).
+template <class R>
+__device__ __forceinline__ int list_atom(const Bufs<R> &B, const Geom &G, int s, int sp, int p, int ld, int cap)
+{
+    using R4 = typename V4<R>::T;
+    int cnt = 0;
+    const double *const xr[3] = {B.xr[s][0], B.xr[s][1], B.xr[s][2]};
+    const R4 *sw = B.shadow[sp];
+    const R lo = g_screen_lo<R>(G), hi = g_screen_hi<R>(G);
+    const R hx = g_h<R>(G, 0), hy = g_h<R>(G, 1), hz = g_h<R>(G, 2);
+    const int nx = G.ncell[0], ny = G.ncell[1], nz = G.ncell[2];
+    const int cell = B.cell[p];
+    const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
+    const R4 up = sw[p];
+    uint32_t *lp = B.list + p;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+        int ez = cz + dz;
+        ez += (ez < 0) ? nz : ((ez >= nz) ? -nz : 0);
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            int ey = cy + dy;
+            ey += (ey < 0) ? ny : ((ey >= ny) ? -ny : 0);
+            const int row = (ez * ny + ey) * nx;
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                int ex = cx + dx;
+                ex += (ex < 0) ? nx : ((ex >= nx) ? -nx : 0);
+                const int e = row + ex;
+                const uint32_t code = list_entry(0u, dx, dy, dz);
+                const R ox = (R)dx * hx - up.x, oy = (R)dy * hy - up.y, oz = (R)dz * hz - up.z;
+                const int q1 = B.cell_start[e + 1];
+                for (int q = B.cell_start[e]; q < q1; ++q) {
+                    const R4 uq = sw[q];
+                    const R ddx = uq.x + ox, ddy = uq.y + oy, ddz = uq.z + oz;
+                    const R r2 = fma(ddz, ddz, fma(ddy, ddy, ddx * ddx));
+                    if (r2 > hi || q == p) continue;
+                    if (r2 < lo || exact_in_list(xr, p, q, G)) {
+                        if (cnt < cap) lp[(size_t)cnt * ld] = (uint32_t)q | code;
+                        ++cnt;
+                    }
+                }
+            }
+        }
+    }
+    B.nnb[p] = min(cnt, cap);
+    if (cnt > cap) atomicOr(&B.st->error, ERR_LIST_OVERFLOW);
+    return cnt;
+}
+
+// Block maximum of the neighbour counts into st->max_nnb (one atomic per
+// block).  All threads must call.
+__device__ __forceinline__ void block_max_nnb(int cnt, int *dst)
+{
+    __shared__ int smax[32];
+    int m = cnt;
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)((blockDim.x + 31) >> 5); ++w) m = max(m, smax[w]);
+        if (m > *(volatile int *)dst) atomicMax(dst, m);
+    }
+    __syncthreads();
+}
+
+// Opening kick and drift of atom i from the forces cached at the last closed
+// step: v += F dt/(2m), x += v dt; record buffer sp ^ 1 gets the new
+// coordinates.  Returns the squared displacement since the last build (FP32).
+template <class R>
+__device__ __forceinline__ float open_atom(const Bufs<R> &B, const Launch &L, int s, int sp, int i)
+{
+    int ti = L.ntypes > 1 ? B.type[s][i] : 0;
+    double kq = L.half_kick[ti];
+    double dn[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double v = B.v[s][a][i];
+        v = fma((double)B.fcache[a][i], kq, v);
+        B.v[s][a][i] = v;
+        dn[a] = fma(v, L.dt, B.d[a][i]);
+        B.d[a][i] = dn[a];
+    }
+    R u0 = B.uref[0][i] + (R)dn[0], u1 = B.uref[1][i] + (R)dn[1], u2 = B.uref[2][i] + (R)dn[2];
+    B.shadow[sp ^ 1][i] = mk4<R>(u0, u1, u2, (R)0);
+    float fx = (float)dn[0], fy = (float)dn[1], fz = (float)dn[2];
+    return fx * fx + fy * fy + fz * fz;
+}
+
+// Sum of partials[slot * stride + b], b < nb, by one block (any size) in a
+// fixed order; the result goes to the DevState field of the slot (0: embedding
+// energy, 1: pair energy, 2: kinetic energy, 3..8: virial).
+__device__ __forceinline__ void reduce_slot(const double *partials, DevState *st, int slot, int nb, int stride)
+{
+    __shared__ double sm[32];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partials[(size_t)slot * stride + b];
+    s = warp_sum_d(s);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[w];
+        if (slot == 0) st->e_embed = t;
+        else if (slot == 1) st->e_pair = t;
+        else if (slot == 2) st->ke = t;
+        else st->virial[slot - 3] = t;
+    }
+    __syncthreads();
+}
+
+}  // namespace
+}  // namespace eammd

@@ -101,13 +101,17 @@ def test_two_types_fp64_and_mixed():
             assert rel(md.virial(), W) < tol
 
 
-@pytest.mark.parametrize("use_graphs", [True, False])
-def test_trajectory_fp64_matches_oracle(c1, use_graphs):
+LAUNCH = {"graphs": dict(use_graphs=True, persistent="off"), "eager": dict(use_graphs=False, persistent="off"),
+          "single_launch": dict(persistent="on")}
+
+
+@pytest.mark.parametrize("launch", ["graphs", "eager", "single_launch"])
+def test_trajectory_fp64_matches_oracle(c1, launch):
     """100 velocity-Verlet steps at dt = 2 fs, compared every 10 steps; the
     forces are also re-checked at the GPU's own positions (same input)."""
     pot = O.Potential(c1.pot)
     ref = O.System(pot, c1.box, c1.pos, c1.vel, c1.types)
-    with binding.MD(c1, precision="fp64", use_graphs=use_graphs) as md:
+    with binding.MD(c1, precision="fp64", **LAUNCH[launch]) as md:
         for block in range(10):
             md.step(10, 2.0)
             ref.step(10, 2.0)
@@ -146,7 +150,7 @@ def test_mixed_trajectory_tracks_fp64(c1):
 def test_graphs_equal_eager_and_runs_are_deterministic(c1, precision):
     out = []
     for use_graphs in (True, False, True):
-        with binding.MD(c1, precision=precision, use_graphs=use_graphs) as md:
+        with binding.MD(c1, precision=precision, use_graphs=use_graphs, persistent="off") as md:
             md.step(37, 2.0)
             pos, vel, _ = md.get_state()
             out.append((pos, vel, md.energy(), md.forces()))
@@ -183,7 +187,7 @@ def test_displacement_triggers_rebuild():
     s = I.thermal_system(I.BCC_TA_LIKE, (10, 10, 10), 0.02, 3000.0, 99)
     pot = O.Potential(s.pot)
     ref = O.System(pot, s.box, s.pos, s.vel, s.types)
-    with binding.MD(s, precision="fp64", rebuild_every=1000) as md:
+    with binding.MD(s, precision="fp64", rebuild_every=1000, persistent="off") as md:
         md.step(60, 4.0)
         ref.step(60, 4.0, rebuild_every=1000)
         assert md.stats()["rebuilds"] == ref.state()["rebuilds"] > 0

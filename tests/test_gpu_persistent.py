@@ -1,0 +1,119 @@
+"""md_step as one cooperative launch (all phases of all steps, blocks meeting
+at grid barriers) against the graph path and the serial FP64 oracle.
+
+The single launch runs the same per-atom device code with the same lanes per
+atom, so positions, velocities and forces must equal the graph path's bitwise
+over trajectories that include list rebuilds (scheduled and triggered by
+displacement); energy sums come from another block partition and agree to
+rounding.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2405_07898_gb300 import binding, inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 2e-5}
+ETOL = {"fp64": 1e-13, "mixed": 1e-9}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def oracle_forces(system, pos):
+    pot = O.Potential(system.pot)
+    return O.eam_eval(pot, O.wrap(pos, system.box), system.box, system.types)[2]
+
+
+def run_pair(system, precision, lanes, calls, dt, **kw):
+    """The same md_step calls on a single-launch and a graph context."""
+    out = []
+    for persistent in ("on", "off"):
+        with binding.MD(system, precision=precision, lanes_per_atom=lanes, persistent=persistent, **kw) as md:
+            st = md.stats()
+            assert (st["persistent_blocks"] > 0) == (persistent == "on")
+            if persistent == "on":
+                assert st["persistent_lanes"] == lanes
+            for nsteps in calls:
+                md.step(nsteps, dt)
+            pos, vel, step = md.get_state()
+            out.append(dict(pos=pos, vel=vel, step=step, forces=md.forces(), energy=md.energy(),
+                            virial=md.virial(), stats=md.stats()))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("lanes", [1, 2, 8])
+def test_single_launch_equals_graphs(precision, lanes):
+    s = I.bcc_2000_fp64()
+    a, b = run_pair(s, precision, lanes, [37, 1, 12], 2.0)
+    np.testing.assert_array_equal(a["pos"], b["pos"])
+    np.testing.assert_array_equal(a["vel"], b["vel"])
+    np.testing.assert_array_equal(a["forces"], b["forces"])
+    assert a["step"] == b["step"] == 50
+    assert a["stats"]["rebuilds"] == b["stats"]["rebuilds"] >= 4
+    for x, y in zip(a["energy"], b["energy"]):
+        assert abs(x - y) <= ETOL[precision] * abs(y)
+    np.testing.assert_allclose(a["virial"], b["virial"], rtol=ETOL[precision] * 100, atol=1e-12)
+    assert rel(a["forces"], oracle_forces(s, a["pos"])) < TOL[precision]
+
+
+def test_single_launch_displacement_rebuilds():
+    """Hot system, rebuild_every 1000: every build is triggered by an atom
+    moving more than skin/2, decided inside the launch."""
+    s = I.thermal_system(I.BCC_TA_LIKE, (10, 10, 10), 0.02, 3000.0, 99)
+    a, b = run_pair(s, "fp64", 2, [60], 4.0, rebuild_every=1000)
+    np.testing.assert_array_equal(a["pos"], b["pos"])
+    assert a["stats"]["rebuilds"] == b["stats"]["rebuilds"] > 0
+    ref = O.System(O.Potential(s.pot), s.box, s.pos, s.vel, s.types)
+    ref.step(60, 4.0, rebuild_every=1000)
+    assert a["stats"]["rebuilds"] == ref.state()["rebuilds"]
+    d = a["pos"] - ref.state()["pos"]
+    d -= s.box * np.round(d / s.box)
+    assert np.abs(d).max() < 1e-9
+
+
+def test_single_launch_two_types_and_uneven_cells():
+    m = I.multi_type_system()
+    a, b = run_pair(m, "mixed", 4, [25], 2.0)
+    np.testing.assert_array_equal(a["pos"], b["pos"])
+    np.testing.assert_array_equal(a["forces"], b["forces"])
+    rng = np.random.default_rng(11)
+    box = np.array([31.0, 27.0, 35.0])
+    pos = rng.random((2600, 3)) * box
+    keep = [0]
+    for i in range(1, len(pos)):
+        d = pos[keep] - pos[i]
+        d -= box * np.round(d / box)
+        if (d * d).sum(1).min() > 1.7**2:
+            keep.append(i)
+    pos = pos[keep]
+    gas = I.System(box=box, pos=pos, vel=rng.normal(scale=0.004, size=pos.shape),
+                   types=np.zeros(len(pos), np.int32), pot=I.johnson_potential(I.BCC_TA_LIKE))
+    a, b = run_pair(gas, "fp64", 1, [30], 1.0)
+    np.testing.assert_array_equal(a["pos"], b["pos"])
+    assert rel(a["forces"], oracle_forces(gas, a["pos"])) < TOL["fp64"]
+
+
+def test_single_launch_after_set_state_and_auto_threshold():
+    s = I.bcc_2000_fp64()
+    with binding.MD(s, precision="fp64") as md:  # auto: 2,000 atoms take the single launch
+        assert md.stats()["persistent_blocks"] > 0
+        md.step(20, 2.0)
+        pos, vel, step = md.get_state()
+        md.step(15, 2.0)
+        p1, v1, _ = md.get_state()
+    with binding.MD(s, precision="fp64", persistent="on") as md:
+        md.set_state(pos, vel, step)
+        md.step(15, 2.0)
+        p2, v2, st2 = md.get_state()
+    assert st2 == 35
+    d = p2 - p1
+    d -= s.box * np.round(d / s.box)
+    assert np.abs(d).max() < 1e-12
+    big = I.bcc_cube(22)  # 21,296 atoms: above the automatic threshold
+    with binding.MD(big, precision="mixed") as md:
+        assert md.stats()["persistent_blocks"] == 0
