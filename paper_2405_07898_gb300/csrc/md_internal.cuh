@@ -171,10 +171,10 @@ struct Launch {
 
 enum StepMode { MODE_MEASURE = 0, MODE_CLOSE = 1, MODE_CLOSE_OPEN = 2 };
 
-// Device words of the persistent step kernel: grid-barrier arrival counter
-// and generation, and the two alternating largest-displacement words.
+// Device words of the persistent step kernel: the grid-barrier arrival
+// counter and the two alternating largest-displacement words.
 struct PersistScratch {
-    unsigned count, gen;
+    unsigned long long arrive;
     unsigned maxdisp[2];
 };
 constexpr int kPersistentBlock = 256;

@@ -8,7 +8,7 @@
 // bitwise equal; energy sums differ in rounding only (other block partition).
 //
 // Grid barriers: all blocks are resident (cooperative launch); a barrier is
-// an arrival counter and a generation word in device memory.  A wait gives up
+// an arrival counter in device memory.  A wait gives up
 // after 1 s of %globaltimer, raises ERR_TIMEOUT and every later barrier of
 // the launch returns at once, so the kernel ends within about a second of a
 // stuck block and the host reports MD_ERR_TIMEOUT.
@@ -27,7 +27,18 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
     return v;
 }
 
-// Returns false once any wait of the launch has timed out.
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(__cvta_generic_to_global(p)) : "memory");
+    return v;
+}
+
+// Grid barrier on a counter that only grows during a launch (zeroed by the
+// host before it): barrier b of the launch is passed once the counter reaches
+// (b + 1) x gridDim.x.  Arrival is a release add, the wait an acquire load, so
+// every block sees the writes all blocks made before the barrier.  Returns
+// false once any wait of the launch has timed out.
 __device__ __forceinline__ bool grid_barrier(PersistScratch *ps, unsigned *err)
 {
     __shared__ int ok;
@@ -37,24 +48,24 @@ __device__ __forceinline__ bool grid_barrier(PersistScratch *ps, unsigned *err)
         if (ld_acquire(err) & ERR_TIMEOUT) {
             good = 0;
         } else {
-            const unsigned g = ld_acquire(&ps->gen);
-            __threadfence();
-            if (atomicAdd(&ps->count, 1u) == gridDim.x - 1) {
-                atomicExch(&ps->count, 0u);
-                __threadfence();
-                atomicAdd(&ps->gen, 1u);
-            } else {
+            unsigned long long a;
+            asm volatile("atom.add.release.gpu.global.u64 %0, [%1], 1;"
+                         : "=l"(a)
+                         : "l"(__cvta_generic_to_global(&ps->arrive))
+                         : "memory");
+            const unsigned long long g = gridDim.x;
+            const unsigned long long target = (a / g + 1) * g;
+            if (a + 1 != target) {
                 const uint64_t t0 = global_ns();
-                while (ld_acquire(&ps->gen) == g) {
+                while (ld_acquire(&ps->arrive) < target) {
                     if ((ld_acquire(err) & ERR_TIMEOUT) || global_ns() - t0 > kWaitLimitNs) {
                         atomicOr(err, ERR_TIMEOUT);
                         good = 0;
                         break;
                     }
-                    __nanosleep(32);
+                    __nanosleep(16);
                 }
             }
-            __threadfence();
         }
         ok = good;
     }
@@ -246,6 +257,8 @@ cudaError_t launch_steps(const Bufs<R> &B, const Geom &G, const Launch &L, long 
     long long ns = nsteps;
     PersistScratch *p = ps;
     void *args[] = {&b, &g, &l, &ns, &p};
+    cudaError_t e = cudaMemsetAsync(&ps->arrive, 0, sizeof(ps->arrive), L.stream);
+    if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPersistentBlock), args, 0, L.stream);
 }
 
