@@ -182,22 +182,28 @@ __device__ __forceinline__ bool stage_list(const uint32_t *list, int ld, int i0,
 
 // This lane's part of rho_i = sum over listed j with r < r_cut of f_{t_j}(r_ij)
 // (Eq. 2).
+// In the force pass the list columns of the first round are read before the
+// neighbour count is known (every column below cap lies inside the list), and
+// those of the next round while this round's records are in flight; columns
+// at or beyond nn are never used to address a record.
 template <class R, bool MULTI, int TPA, int U, class List, class Fetch, class Tab>
-__device__ __forceinline__ R density_lane(const Bufs<R> &B, const R (&h)[3], R rc2, int s, int nn,
-                                          int l, const typename V4<R>::T &ui, const List &list, const Fetch &fetch,
-                                          const Tab &tab)
+__device__ __forceinline__ R density_lane(const Bufs<R> &B, const R (&h)[3], R rc2, int s, const int *nnb_i,
+                                          int cap, int l, const typename V4<R>::T &ui, const List &list,
+                                          const Fetch &fetch, const Tab &tab)
 {
     using R4 = typename V4<R>::T;
     const Tables<R> &T = *B.tables;
     const SplineDesc<R> g = MULTI ? T.f[0] : T.fphi;
     R rho = (R)0;
+    (void)cap;
+    const int nn = *nnb_i;
     // U pairs per round (columns k, k + TPA, ...), all gathers issued before
     // any is used; the sum runs in column order
     for (int k = l; k < nn; k += U * TPA) {
         uint32_t e[U];
-        R4 u[U];
 #pragma unroll
         for (int q = 0; q < U; ++q) e[q] = (k + q * TPA < nn) ? list(k + q * TPA) : 0u;
+        R4 u[U];
 #pragma unroll
         for (int q = 0; q < U; ++q) u[q] = fetch(q == 0 || k + q * TPA < nn ? e[q] : e[0]);
 #pragma unroll
@@ -242,7 +248,7 @@ __device__ __forceinline__ R embed(const Bufs<R> &B, typename V4<R>::T *sw, int 
 // W xx yy zz xy xz yz).
 template <class R, bool MULTI, bool ENERGY, int TPA, int U, class List, class Fetch, class Tab>
 __device__ __forceinline__ void force_lane(const Bufs<R> &B, const Launch &L, const R (&h)[3], R rc2,
-                                           int s, int nn, int l, int ti, const typename V4<R>::T &ui,
+                                           int s, const int *nnb_i, int l, int ti, const typename V4<R>::T &ui,
                                            const List &list, const Fetch &fetch, R (&f)[3], R (&e7)[7],
                                            const Tab &tab)
 {
@@ -250,13 +256,17 @@ __device__ __forceinline__ void force_lane(const Bufs<R> &B, const Launch &L, co
     const Tables<R> &T = *B.tables;
     const SplineDesc<R> g = T.fphi;
     const R Fpi = ui.w;
+    uint32_t e[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) e[q] = (l + q * TPA < L.cap) ? list(l + q * TPA) : 0u;
+    const int nn = *nnb_i;
     for (int k = l; k < nn; k += U * TPA) {
-        uint32_t e[U];
         R4 u[U];
 #pragma unroll
-        for (int q = 0; q < U; ++q) e[q] = (k + q * TPA < nn) ? list(k + q * TPA) : 0u;
-#pragma unroll
         for (int q = 0; q < U; ++q) u[q] = fetch(q == 0 || k + q * TPA < nn ? e[q] : e[0]);
+        uint32_t en[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) en[q] = (k + (U + q) * TPA < nn) ? list(k + (U + q) * TPA) : 0u;
 #pragma unroll
         for (int q = 0; q < U; ++q) {
             const PairIn<R> p = pair_vector<R>(ui, u[q], entry_shift<R>(e[q], h));
@@ -298,6 +308,8 @@ __device__ __forceinline__ void force_lane(const Bufs<R> &B, const Launch &L, co
                 }
             }
         }
+#pragma unroll
+        for (int q = 0; q < U; ++q) e[q] = en[q];
     }
 }
 
@@ -424,12 +436,11 @@ __global__ void __launch_bounds__(256) k_density(Bufs<R> B, Geom G, Launch L)
     const R rc2 = g_rc2<R>(G);
     R rho = (R)0;
     if (active) {
-        const int nn = B.nnb[i];
         if (tiled)
-            rho = density_lane<R, MULTI, TPA, U>(B, h, rc2, s, nn, l, sw[i], ListTile{tile + (i - i0), width},
+            rho = density_lane<R, MULTI, TPA, U>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], ListTile{tile + (i - i0), width},
                                                  GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2});
         else
-            rho = density_lane<R, MULTI, TPA, U>(B, h, rc2, s, nn, l, sw[i], ListGlobal{B.list + i, L.ld},
+            rho = density_lane<R, MULTI, TPA, U>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], ListGlobal{B.list + i, L.ld},
                                                  GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2});
     }
     rho = lane_sum<TPA>(rho);
@@ -463,12 +474,11 @@ __global__ void __launch_bounds__(256) k_force(Bufs<R> B, Geom G, Launch L)
     R f[3] = {0, 0, 0};
     R e7[7] = {0, 0, 0, 0, 0, 0, 0};
     if (active) {
-        const int nn = B.nnb[i];
         if (tiled)
-            force_lane<R, MULTI, ENERGY, TPA, U>(B, L, h, rc2, s, nn, l, ti, sw[i], ListTile{tile + (i - i0), width},
+            force_lane<R, MULTI, ENERGY, TPA, U>(B, L, h, rc2, s, B.nnb + i, l, ti, sw[i], ListTile{tile + (i - i0), width},
                                                  GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2});
         else
-            force_lane<R, MULTI, ENERGY, TPA, U>(B, L, h, rc2, s, nn, l, ti, sw[i], ListGlobal{B.list + i, L.ld},
+            force_lane<R, MULTI, ENERGY, TPA, U>(B, L, h, rc2, s, B.nnb + i, l, ti, sw[i], ListGlobal{B.list + i, L.ld},
                                                  GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2});
     }
 #pragma unroll
@@ -540,13 +550,12 @@ __global__ void __launch_bounds__(256) k_density_rows(Bufs<R> B, Geom G, Launch 
         const bool active = i < a1;
         R rho = (R)0;
         if (active) {
-            const int nn = B.nnb[i];
-            const ListGlobal list{B.list + i, L.ld};
+                const ListGlobal list{B.list + i, L.ld};
             if (staged)
-                rho = density_lane<R, false, TPA, 4>(B, h, rc2, s, nn, l, stage[i - base[4]], list,
+                rho = density_lane<R, false, TPA, 4>(B, h, rc2, s, B.nnb + i, L.cap, l, stage[i - base[4]], list,
                                                      StagedFetch<R>{stage, base}, TabGlobal<R>{B.coef2});
             else
-                rho = density_lane<R, false, TPA, 4>(B, h, rc2, s, nn, l, sw[i], list, GlobalFetch<R>{sw},
+                rho = density_lane<R, false, TPA, 4>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], list, GlobalFetch<R>{sw},
                                                      TabGlobal<R>{B.coef2});
         }
         rho = lane_sum<TPA>(rho);
@@ -582,13 +591,12 @@ __global__ void __launch_bounds__(256) k_force_rows(Bufs<R> B, Geom G, Launch L)
         const bool active = i < a1;
         R f[3] = {0, 0, 0};
         if (active) {
-            const int nn = B.nnb[i];
-            const ListGlobal list{B.list + i, L.ld};
+                const ListGlobal list{B.list + i, L.ld};
             if (staged)
-                force_lane<R, false, ENERGY, TPA, 4>(B, L, h, rc2, s, nn, l, 0, stage[i - base[4]], list,
+                force_lane<R, false, ENERGY, TPA, 4>(B, L, h, rc2, s, B.nnb + i, l, 0, stage[i - base[4]], list,
                                                      StagedFetch<R>{stage, base}, f, e7, TabGlobal<R>{B.coef2});
             else
-                force_lane<R, false, ENERGY, TPA, 4>(B, L, h, rc2, s, nn, l, 0, sw[i], list, GlobalFetch<R>{sw}, f,
+                force_lane<R, false, ENERGY, TPA, 4>(B, L, h, rc2, s, B.nnb + i, l, 0, sw[i], list, GlobalFetch<R>{sw}, f,
                                                      e7, TabGlobal<R>{B.coef2});
         }
 #pragma unroll
@@ -637,7 +645,7 @@ __global__ void __launch_bounds__(256) k_density_tab(Bufs<float> B, Geom G, Laun
         const bool active = i < L.n;
         float rho = 0.f;
         if (active)
-            rho = density_lane<float, false, TPA, 2>(B, h, rc2, s, B.nnb[i], l, sw[i], ListGlobal{B.list + i, L.ld},
+            rho = density_lane<float, false, TPA, 2>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], ListGlobal{B.list + i, L.ld},
                                                      GlobalFetch<float>{sw}, tab);
         rho = lane_sum<TPA>(rho);
         if (active && l == 0) e_embed += embed<float>(B, sw, i, 0, rho);
@@ -673,7 +681,7 @@ __global__ void __launch_bounds__(256) k_force_tab(Bufs<float> B, Geom G, Launch
         const bool active = i < L.n;
         float f[3] = {0, 0, 0};
         if (active)
-            force_lane<float, false, ENERGY, TPA, 2>(B, L, h, rc2, s, B.nnb[i], l, 0, sw[i],
+            force_lane<float, false, ENERGY, TPA, 2>(B, L, h, rc2, s, B.nnb + i, l, 0, sw[i],
                                                      ListGlobal{B.list + i, L.ld}, GlobalFetch<float>{sw}, f, e7, tab);
 #pragma unroll
         for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);

@@ -20,6 +20,11 @@
 namespace eammd {
 namespace {
 
+__device__ __forceinline__ void prefetch_l1(const void *p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(__cvta_generic_to_global(p)));
+}
+
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
 {
     unsigned v;
@@ -148,7 +153,7 @@ __global__ void __launch_bounds__(256) k_steps(Bufs<R> B, Geom G, Launch L, long
                 const int ti = (MULTI && active) ? B.type[s][i] : 0;
                 R rho = (R)0;
                 if (active)
-                    rho = density_lane<R, MULTI, TPA, UD>(B, h, rc2, s, B.nnb[i], l, sw[i], ListGlobal{B.list + i, L.ld},
+                    rho = density_lane<R, MULTI, TPA, UD>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], ListGlobal{B.list + i, L.ld},
                                                           GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2});
                 rho = lane_sum<TPA>(rho);
                 if (active && l == 0) e_embed += embed<R>(B, sw, i, ti, rho);
@@ -174,16 +179,25 @@ __global__ void __launch_bounds__(256) k_steps(Bufs<R> B, Geom G, Launch L, long
                 R f[3] = {0, 0, 0};
                 float d2 = 0.f;
                 const ListGlobal list{B.list + i, L.ld};
+                // the integration's inputs into L1 while the pair loop runs
+                if (active && l == 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        prefetch_l1(B.v[s][c] + i);
+                        prefetch_l1(B.d[c] + i);
+                        prefetch_l1(B.uref[c] + i);
+                    }
+                }
                 if (last) {
                     if (active)
-                        force_lane<R, MULTI, true, TPA, UF>(B, L, h, rc2, s, B.nnb[i], l, ti, sw[i], list,
+                        force_lane<R, MULTI, true, TPA, UF>(B, L, h, rc2, s, B.nnb + i, l, ti, sw[i], list,
                                                             GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2});
 #pragma unroll
                     for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);
                     if (active) integrate<R, MODE_CLOSE, true, TPA>(B, L, s, sp, i, l, ti, f, ke, d2);
                 } else {
                     if (active)
-                        force_lane<R, MULTI, false, TPA, UF>(B, L, h, rc2, s, B.nnb[i], l, ti, sw[i], list,
+                        force_lane<R, MULTI, false, TPA, UF>(B, L, h, rc2, s, B.nnb + i, l, ti, sw[i], list,
                                                              GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2});
 #pragma unroll
                     for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);
