@@ -183,9 +183,9 @@ __device__ __forceinline__ bool stage_list(const uint32_t *list, int ld, int i0,
 // This lane's part of rho_i = sum over listed j with r < r_cut of f_{t_j}(r_ij)
 // (Eq. 2).
 // In the force pass the list columns of the first round are read before the
-// neighbour count is known (every column below cap lies inside the list), and
-// those of the next round while this round's records are in flight; columns
-// at or beyond nn are never used to address a record.
+// neighbour count is known (every column below cap lies inside the list);
+// while a round is computed, the next round's records and the columns of the
+// round after are in flight.  Columns at or beyond nn never address a record.
 template <class R, bool MULTI, int TPA, int U, class List, class Fetch, class Tab>
 __device__ __forceinline__ R density_lane(const Bufs<R> &B, const R (&h)[3], R rc2, int s, const int *nnb_i,
                                           int cap, int l, const typename V4<R>::T &ui, const List &list,
@@ -256,17 +256,26 @@ __device__ __forceinline__ void force_lane(const Bufs<R> &B, const Launch &L, co
     const Tables<R> &T = *B.tables;
     const SplineDesc<R> g = T.fphi;
     const R Fpi = ui.w;
-    uint32_t e[U];
+    constexpr int W = U * TPA;  // columns per round
+    uint32_t e[U], en[U];
+    R4 u[U];
 #pragma unroll
     for (int q = 0; q < U; ++q) e[q] = (l + q * TPA < L.cap) ? list(l + q * TPA) : 0u;
     const int nn = *nnb_i;
-    for (int k = l; k < nn; k += U * TPA) {
-        R4 u[U];
 #pragma unroll
-        for (int q = 0; q < U; ++q) u[q] = fetch(q == 0 || k + q * TPA < nn ? e[q] : e[0]);
-        uint32_t en[U];
+    for (int q = 0; q < U; ++q) en[q] = (l + W + q * TPA < nn) ? list(l + W + q * TPA) : 0u;
 #pragma unroll
-        for (int q = 0; q < U; ++q) en[q] = (k + (U + q) * TPA < nn) ? list(k + (U + q) * TPA) : 0u;
+    for (int q = 0; q < U; ++q) u[q] = (l < nn) ? fetch(q == 0 || l + q * TPA < nn ? e[q] : e[0]) : ui;
+    for (int k = l; k < nn; k += W) {
+        // in flight while this round is computed: the next round's records
+        // and the columns of the round after
+        const int k1 = k + W;
+        R4 un[U];
+        uint32_t e2[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) un[q] = (k1 < nn) ? fetch(q == 0 || k1 + q * TPA < nn ? en[q] : en[0]) : ui;
+#pragma unroll
+        for (int q = 0; q < U; ++q) e2[q] = (k1 + W + q * TPA < nn) ? list(k1 + W + q * TPA) : 0u;
 #pragma unroll
         for (int q = 0; q < U; ++q) {
             const PairIn<R> p = pair_vector<R>(ui, u[q], entry_shift<R>(e[q], h));
@@ -309,7 +318,11 @@ __device__ __forceinline__ void force_lane(const Bufs<R> &B, const Launch &L, co
             }
         }
 #pragma unroll
-        for (int q = 0; q < U; ++q) e[q] = en[q];
+        for (int q = 0; q < U; ++q) {
+            e[q] = en[q];
+            en[q] = e2[q];
+            u[q] = un[q];
+        }
     }
 }
 
