@@ -129,6 +129,18 @@ __device__ __forceinline__ Shift<R> entry_shift(uint32_t e, const R (&h)[3])
 {
     return Shift<R>{axis_shift<R>(e, 0, h[0]), axis_shift<R>(e, 1, h[1]), axis_shift<R>(e, 2, h[2])};
 }
+// FP32: t in {0, 1, 2} placed in the low mantissa bits of 1.5 * 2^23 gives
+// the float 1.5 * 2^23 + t exactly; subtracting 1.5 * 2^23 + 1 leaves t - 1 in
+// {-1, 0, 1} exactly, and (t - 1) * h is the same -h, 0 or h as above.
+template <>
+__device__ __forceinline__ Shift<float> entry_shift<float>(uint32_t e, const float (&h)[3])
+{
+    const uint32_t c = e >> kCodeShift;
+    const float mx = __uint_as_float((c & 3u) | 0x4B400000u) - 12582913.0f;
+    const float my = __uint_as_float(((c >> 2) & 3u) | 0x4B400000u) - 12582913.0f;
+    const float mz = __uint_as_float((c >> 4) | 0x4B400000u) - 12582913.0f;
+    return Shift<float>{mx * h[0], my * h[1], mz * h[2]};
+}
 // Row (dz + 1) * 3 + (dy + 1) of the 3 x 3 rows of cells around an atom's
 // row that a list entry's neighbour lives in.
 __device__ __forceinline__ int entry_row(uint32_t e)
