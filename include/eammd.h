@@ -140,7 +140,7 @@ enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2, MD_SCH
  *                    back to MD_SCHEDULE_ATOMS where it does not apply.
  *   persistent       MD_PERSIST_AUTO (0): md_step runs as one cooperative
  *                    launch (all phases of all steps, blocks meeting at grid
- *                    barriers) for systems of at most 20,000 atoms, else as
+ *                    barriers) for systems of at most 65,536 atoms, else as
  *                    CUDA graphs.  MD_PERSIST_OFF: always the graph (or
  *                    eager) path.  MD_PERSIST_ON: always the single launch.
  *                    Lanes per atom of the single launch: lanes_per_atom, or

@@ -784,7 +784,7 @@ md_status autotune(md_ctx *ctx)
 // Threshold of MD_PERSIST_AUTO: at and below this many atoms a step is a few
 // microseconds of work and one cooperative launch per md_step call beats the
 // graph replay (measured on GB300 over the BCC sweep).
-constexpr int64_t kPersistentAutoAtoms = 20000;
+constexpr int64_t kPersistentAutoAtoms = 65536;
 
 // The persistent step launch: lanes per atom (from the options, else timed
 // over 1, 2, 4, 8 on rebuild_every - 1 steps at dt = 0, which moves no atom

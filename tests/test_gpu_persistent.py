@@ -114,6 +114,6 @@ def test_single_launch_after_set_state_and_auto_threshold():
     d = p2 - p1
     d -= s.box * np.round(d / s.box)
     assert np.abs(d).max() < 1e-12
-    big = I.bcc_cube(22)  # 21,296 atoms: above the automatic threshold
+    big = I.bcc_cube(33)  # 71,874 atoms: above the automatic threshold
     with binding.MD(big, precision="mixed") as md:
         assert md.stats()["persistent_blocks"] == 0
