@@ -433,19 +433,29 @@ __device__ void run_replica(const BatchBufs &B, Smem &S, int r, int mode, int ns
             const int nn = B.nnb[P.atom_off + i];
             const uint32_t *lp = B.list + P.list_off + i;
             float rho = 0.f;
-            for (int k = 0; k < nn; ++k) {
-                const uint32_t e = lp[(size_t)k * P.ld];
-                const float4 uj = sw[e & kIndexMask];
-                const Shift<float> shf = entry_shift<float>(e, hf);
-                const float dx = (uj.x - ui.x) + shf.x, dy = (uj.y - ui.y) + shf.y, dz = (uj.z - ui.z) + shf.z;
-                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                if (r2 < P.rc2_f) {
-                    float rinv, rr;
-                    inv_r(r2, rinv, rr);
-                    float t;
-                    const int kk = segment(g, rr, t);
-                    const float4 c = cf2[2 * (g.offset + kk)];
-                    rho += fmaf(t, fmaf(t, fmaf(t, c.w, c.z), c.y), c.x);
+            // four pairs per round, all gathers issued before any is used;
+            // the sum runs in column order
+            for (int k = 0; k < nn; k += 4) {
+                uint32_t e[4];
+                float4 u[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) e[q] = (k + q < nn) ? lp[(size_t)(k + q) * P.ld] : 0u;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) u[q] = sw[(q == 0 || k + q < nn ? e[q] : e[0]) & kIndexMask];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const Shift<float> shf = entry_shift<float>(e[q], hf);
+                    const float dx = (u[q].x - ui.x) + shf.x, dy = (u[q].y - ui.y) + shf.y,
+                                dz = (u[q].z - ui.z) + shf.z;
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    if (k + q < nn && r2 < P.rc2_f) {
+                        float rinv, rr;
+                        inv_r(r2, rinv, rr);
+                        float t;
+                        const int kk = segment(g, rr, t);
+                        const float4 c = cf2[2 * (g.offset + kk)];
+                        rho += fmaf(t, fmaf(t, fmaf(t, c.w, c.z), c.y), c.x);
+                    }
                 }
             }
             float Fv, Fdv;
@@ -465,13 +475,31 @@ __device__ void run_replica(const BatchBufs &B, Smem &S, int r, int mode, int ns
             const int nn = B.nnb[gi];
             const uint32_t *lp = B.list + P.list_off + i;
             float fx = 0.f, fy = 0.f, fz = 0.f;
-            for (int k = 0; k < nn; ++k) {
-                const uint32_t e = lp[(size_t)k * P.ld];
-                const float4 uj = sw[e & kIndexMask];
-                const Shift<float> shf = entry_shift<float>(e, hf);
+            // two pairs per round; the next round's records and the columns
+            // of the round after are in flight while a round is computed
+            uint32_t e[2], en[2];
+            float4 u[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) e[q] = (q < nn) ? lp[(size_t)q * P.ld] : 0u;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) en[q] = (2 + q < nn) ? lp[(size_t)(2 + q) * P.ld] : 0u;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) u[q] = (nn > 0) ? sw[(q == 0 || q < nn ? e[q] : e[0]) & kIndexMask] : ui;
+            for (int k = 0; k < nn; k += 2) {
+                float4 un[2];
+                uint32_t e2[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                    un[q] = (k + 2 < nn) ? sw[(q == 0 || k + 2 + q < nn ? en[q] : en[0]) & kIndexMask] : ui;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) e2[q] = (k + 4 + q < nn) ? lp[(size_t)(k + 4 + q) * P.ld] : 0u;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                const float4 uj = u[q];
+                const Shift<float> shf = entry_shift<float>(e[q], hf);
                 const float dx = (uj.x - ui.x) + shf.x, dy = (uj.y - ui.y) + shf.y, dz = (uj.z - ui.z) + shf.z;
                 const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                if (r2 < P.rc2_f) {
+                if (k + q < nn && r2 < P.rc2_f) {
                     float rinv, rr;
                     inv_r(r2, rinv, rr);
                     float t;
@@ -486,6 +514,13 @@ __device__ void run_replica(const BatchBufs &B, Smem &S, int r, int mode, int ns
                     fy = fmaf(sr, dy, fy);
                     fz = fmaf(sr, dz, fz);
                     if (energy) e_pair += 0.5f * fmaf(t, fmaf(t, fmaf(t, cp.w, cp.z), cp.y), cp.x);
+                }
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    e[q] = en[q];
+                    en[q] = e2[q];
+                    u[q] = un[q];
                 }
             }
             if (!isfinite(fx + fy + fz)) atomicOr(&st->error, ERR_NONFINITE);
