@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_2405_07898_gb300 import binding, build
@@ -65,3 +66,40 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu():
     with pytest.raises(binding.MDError) as e:
         binding.MD(wrong_type, use_torch=False)
     assert e.value.status == -1  # MD_ERR_ARG
+
+
+@pytest.mark.parametrize("kw", [dict(lanes_per_atom=3), dict(block_size=100), dict(block_size=512),
+                                dict(schedule="rows", lanes_per_atom=8), dict(schedule="table", lanes_per_atom=8),
+                                dict(stage_capacity=-1)])
+def test_create_rejects_bad_options_before_touching_the_gpu(kw):
+    from paper_2405_07898_gb300 import inputs as I
+    s = I.bcc_2000_fp64()
+    with pytest.raises(binding.MDError) as e:
+        binding.MD(s, use_torch=False, **kw)
+    assert e.value.status == -1  # MD_ERR_ARG
+
+
+def test_create_rejects_out_of_range_enums():
+    """schedule and persistent outside their enumerations (set in the raw
+    options struct, past what the Python names allow)."""
+    from paper_2405_07898_gb300 import inputs as I
+    s = I.bcc_2000_fp64()
+    lib = binding.load()
+    class Holder:
+        _keep = []
+
+    pc = binding.MD._potential_c(Holder(), s.pot)
+    box = np.ascontiguousarray(s.box, dtype=np.float64)
+    pos = np.ascontiguousarray(s.pos, dtype=np.float64)
+    types = np.ascontiguousarray(s.types, dtype=np.int32)
+    dp = ctypes.POINTER(ctypes.c_double)
+    for field, value in (("schedule", 5), ("persistent", 3), ("precision", 2)):
+        opt = binding.Options()
+        lib.md_options_default(ctypes.byref(opt))
+        setattr(opt, field, value)
+        h = ctypes.c_void_p()
+        rc = lib.md_create(box.ctypes.data_as(dp), s.n, pos.ctypes.data_as(dp), None,
+                           types.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(pc),
+                           ctypes.byref(opt), ctypes.byref(h))
+        assert rc == -1, (field, rc, lib.md_last_error(None))
+        assert not h.value
