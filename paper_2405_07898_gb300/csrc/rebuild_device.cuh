@@ -146,19 +146,14 @@ __device__ __forceinline__ bool exact_in_list(const double *const xr[3], int p, 
     return r2 < G.rl2;
 }
 
-// Verlet list: for each atom the atoms of the 27 surrounding cells (in
-// stencil order, ascending id inside a cell) closer than r_list.  The test
-// runs in R on the cell-centred coordinates; candidates within the rounding
-// margin of r_list are decided by exact_in_list, so the list is bit-identical
-// to the FP64 definition.  The stencil loop is unrolled: cell codes and
-// shifts are constants of each unrolled iteration.
 // Verlet list of atom p: the atoms of the 27 surrounding cells (in stencil
 // order, ascending id inside a cell) closer than r_list.  The test runs in R
 // on the cell-centred coordinates; candidates within the rounding margin of
 // r_list are decided by exact_in_list, so the list is bit-identical to the
-// FP64 definition.  The stencil loop is unrolled: cell offsets and shifts are
-// constants of each unrolled iteration.  Returns the neighbour count (the
-// list keeps at most cap of them; more raises ERR_LIST_OVERFLOW).
+// FP64 definition.  The 9 rows of the stencil are unrolled; the 3 cells of a
+// row are a loop (a fully unrolled stencil outgrows the instruction cache).
+// Returns the neighbour count (the list keeps at most cap of them; more
+// raises ERR_LIST_OVERFLOW).
 template <class R>
 __device__ __forceinline__ int list_atom(const Bufs<R> &B, const Geom &G, int s, int sp, int p, int ld, int cap)
 {
@@ -182,7 +177,7 @@ __device__ __forceinline__ int list_atom(const Bufs<R> &B, const Geom &G, int s,
             int ey = cy + dy;
             ey += (ey < 0) ? ny : ((ey >= ny) ? -ny : 0);
             const int row = (ez * ny + ey) * nx;
-#pragma unroll
+#pragma unroll 1
             for (int dx = -1; dx <= 1; ++dx) {
                 int ex = cx + dx;
                 ex += (ex < 0) ? nx : ((ex >= nx) ? -nx : 0);
