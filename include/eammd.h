@@ -209,7 +209,11 @@ md_status md_virial(md_ctx *ctx, double w[6]);
 md_status md_get_state(md_ctx *ctx, double *pos, double *vel, int64_t *step);
 
 /* Replace positions and velocities (original order), rebuild the list and
- * re-evaluate forces and energies.  vel may be NULL for zero. */
+ * re-evaluate forces and energies.  vel may be NULL for zero.  pos and vel
+ * are host arrays (pinned memory makes the copy asynchronous DMA).
+ * Synchronises.  Errors: MD_ERR_ARG (pos NULL); MD_ERR_NONFINITE when a
+ * value is not finite (checked on the device while loading; the context's
+ * state is then undefined until the next successful md_set_state). */
 md_status md_set_state(md_ctx *ctx, const double *pos, const double *vel, int64_t step);
 
 /* Neighbour list of the last build in original atom ids, CSR:

@@ -1297,9 +1297,7 @@ md_status md_set_state(md_ctx *ctx, const double *pos, const double *vel, int64_
         return MD_OK;
     }
     if (!pos) return ctx->fail(MD_ERR_ARG, "pos is NULL");
-    for (int64_t i = 0; i < 3 * ctx->n; ++i)
-        if (!std::isfinite(pos[i]) || (vel && !std::isfinite(vel[i])))
-            return ctx->fail(MD_ERR_NONFINITE, "non-finite position or velocity");
+    // finiteness is checked on the device as the state is loaded
     return ctx->precision == MD_PRECISION_MIXED ? load_and_measure<float>(ctx, pos, vel, step)
                                                 : load_and_measure<double>(ctx, pos, vel, step);
 }

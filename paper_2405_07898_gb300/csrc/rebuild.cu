@@ -187,12 +187,17 @@ __global__ void k_load_state(Bufs<R> B, const double *pos, const double *vel, co
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int s = B.st->set;
+    bool finite = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        B.xr[s][a][i] = pos[3 * (size_t)i + a];
+        const double x = pos[3 * (size_t)i + a];
+        const double v = vel ? vel[3 * (size_t)i + a] : 0.0;
+        finite = finite && isfinite(x) && isfinite(v);
+        B.xr[s][a][i] = x;
         B.d[a][i] = 0.0;
-        B.v[s][a][i] = vel ? vel[3 * (size_t)i + a] : 0.0;
+        B.v[s][a][i] = v;
     }
+    if (!finite) atomicOr(&B.st->error, ERR_NONFINITE);
     B.id[s][i] = i;
     B.type[s][i] = types[i];
 }

@@ -181,6 +181,28 @@ def test_set_state_roundtrip_and_resume(c1):
     assert np.abs(v2 - ref_vel).max() < 1e-13
 
 
+def test_set_state_rejects_non_finite_and_recovers(c1):
+    """Non-finite positions or velocities are caught on the device while the
+    state loads (MD_ERR_NONFINITE); the next valid md_set_state recovers."""
+    with binding.MD(c1, precision="mixed") as md:
+        pos, vel, step = md.get_state()
+        bad = pos.copy()
+        bad[7, 2] = np.nan
+        with pytest.raises(binding.MDError) as e:
+            md.set_state(bad, vel, step)
+        assert e.value.status == -5
+        badv = vel.copy()
+        badv[3, 0] = np.inf
+        with pytest.raises(binding.MDError) as e:
+            md.set_state(pos, badv, step)
+        assert e.value.status == -5
+        md.set_state(pos, vel, step)
+        md.step(10, 2.0)
+        p2, _, _ = md.get_state()
+        _, _, F, _, _ = oracle_eval(c1, p2)
+        assert rel(md.forces(), F) < MIXED_TOL
+
+
 def test_displacement_triggers_rebuild():
     """At high temperature atoms cross skin/2 before 10 steps: the list is
     rebuilt on the device as in the oracle, and forces stay exact."""
