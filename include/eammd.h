@@ -150,6 +150,9 @@ enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2, MD_SCH
  *                    lanes per atom; energy sums differ in rounding only.  A
  *                    grid-barrier wait longer than 1 s ends the launch and
  *                    raises MD_ERR_TIMEOUT.
+ *   wait_limit_us    longest device-side wait (a grid barrier of the single
+ *                    launch, the bulk-copy barrier of list tiles) before the
+ *                    kernel gives up and raises MD_ERR_TIMEOUT; 0 = 1 s.
  *   stage_capacity   records a row-staged block holds; 0 = 1.1 x the most
  *                    that any 3 x 3 block of rows holds at md_create, + 32.
  *                    Must fit the shared memory of a block (160 KB of
@@ -168,6 +171,7 @@ typedef struct {
     int32_t schedule;
     int32_t stage_capacity;
     int32_t persistent;
+    int32_t wait_limit_us;
 } md_options;
 
 void md_options_default(md_options *opt);

@@ -57,7 +57,8 @@ class Options(C.Structure):
                 ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("schedule", C.c_int32),
                 ("stage_capacity", C.c_int32),
-                ("persistent", C.c_int32)]
+                ("persistent", C.c_int32),
+                ("wait_limit_us", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -223,7 +224,7 @@ class MD:
     def __init__(self, system, precision: str = "mixed", rebuild_every: int = 10,
                  list_capacity: int = 0, use_graphs: bool = True, block_size: int = 256,
                  lanes_per_atom: int = 0, use_torch: bool | None = None, schedule: str = "auto",
-                 stage_capacity: int = 0, persistent: str = "auto"):
+                 stage_capacity: int = 0, persistent: str = "auto", wait_limit_us: int = 0):
         L = load()
         self._L = L
         self.n = int(system.n)
@@ -239,6 +240,7 @@ class MD:
         opt.schedule = SCHEDULE[schedule]
         opt.stage_capacity = stage_capacity
         opt.persistent = PERSIST[persistent]
+        opt.wait_limit_us = wait_limit_us
         self._keep = []
         if use_torch is None:
             try:

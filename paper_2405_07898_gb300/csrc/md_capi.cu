@@ -1137,6 +1137,7 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     if (o.stage_capacity < 0) return bad(MD_ERR_ARG, "stage_capacity must be >= 0");
     if (o.persistent < MD_PERSIST_AUTO || o.persistent > MD_PERSIST_ON)
         return bad(MD_ERR_ARG, "persistent must be MD_PERSIST_AUTO, _OFF or _ON");
+    if (o.wait_limit_us < 0) return bad(MD_ERR_ARG, "wait_limit_us must be >= 0");
 
     md_ctx *ctx = new (std::nothrow) md_ctx();
     if (!ctx) return bad(MD_ERR_OOM, "host allocation failed");
@@ -1201,6 +1202,7 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     L.rebuild_every = o.rebuild_every;
     L.disp2_thr = 0.25 * pot->skin * pot->skin;
     L.stream = ctx->stream;
+    L.wait_ns = 1000ull * (unsigned long long)(o.wait_limit_us > 0 ? o.wait_limit_us : 1000000);
     for (int t = 0; t < pot->ntypes; ++t) L.ke_factor[t] = 0.5 * pot->mass[t] / kAccel;
     if (o.list_capacity > 0) {
         L.cap = o.list_capacity;

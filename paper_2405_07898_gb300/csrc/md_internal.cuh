@@ -167,6 +167,7 @@ struct Launch {
     cudaStream_t stream;
     cudaGraphConditionalHandle cond;  // 0 outside graph capture
     int use_cond;
+    unsigned long long wait_ns;       // limit of a device-side wait (grid barrier, bulk-copy barrier)
 };
 
 enum StepMode { MODE_MEASURE = 0, MODE_CLOSE = 1, MODE_CLOSE_OPEN = 2 };

@@ -142,16 +142,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
     }
 }
 
-constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s: for copies still in flight after a timeout
 
 // Columns 0 .. ncol-1 of the list of atoms [i0, i0 + width) into the block's
 // tile (column k at tile + k * width) by bulk asynchronous copies, one per
 // column, that complete on one mbarrier.  Every column is a contiguous,
 // 128-byte aligned run of the list (ld and width are multiples of 32 atoms).
 // Returns false (and flags ERR_TIMEOUT) if the copies did not land within
-// the wait limit; the caller then reads the list from device memory.
+// wait_ns; the caller then reads the list from device memory.
 __device__ __forceinline__ bool stage_list(const uint32_t *list, int ld, int i0, int width, int ncol,
-                                           uint32_t *tile, unsigned int *err)
+                                           uint32_t *tile, unsigned int *err, uint64_t wait_ns)
 {
     __shared__ __align__(8) uint64_t bar;
     const uint32_t bar_a = (uint32_t)__cvta_generic_to_shared(&bar);
@@ -174,7 +174,7 @@ __device__ __forceinline__ bool stage_list(const uint32_t *list, int ld, int i0,
                 : "memory");
         }
     }
-    if (mbar_wait(bar_a, 0, kWaitLimitNs)) return true;
+    if (mbar_wait(bar_a, 0, wait_ns)) return true;
     atomicOr(err, ERR_TIMEOUT);
     mbar_wait(bar_a, 0, kWaitLimitNs);  // the copies still own the tile
     return false;
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(256) k_density(Bufs<R> B, Geom G, Launch L)
     const int i0 = blockIdx.x * width;
     uint32_t *tile = reinterpret_cast<uint32_t *>(dyn);
     if (!LS) prefetch_warp_streams<R, false>(B, L, s, i0 + (threadIdx.x >> 5) * (32 / TPA), 32 / TPA, min(st->max_nnb, L.cap));
-    const bool tiled = LS && stage_list(B.list, L.ld, i0, width, min(st->max_nnb, L.cap), tile, &B.st->error);
+    const bool tiled = LS && stage_list(B.list, L.ld, i0, width, min(st->max_nnb, L.cap), tile, &B.st->error, L.wait_ns);
     const int i = i0 + threadIdx.x / TPA, l = threadIdx.x % TPA;
     const bool active = i < L.n;
     const int ti = (MULTI && active) ? B.type[s][i] : 0;
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(256) k_force(Bufs<R> B, Geom G, Launch L)
     const int i0 = blockIdx.x * width;
     uint32_t *tile = reinterpret_cast<uint32_t *>(dyn);
     prefetch_warp_streams<R, true>(B, L, s, i0 + (threadIdx.x >> 5) * (32 / TPA), 32 / TPA, LS ? 0 : min(st->max_nnb, L.cap));
-    const bool tiled = LS && stage_list(B.list, L.ld, i0, width, min(st->max_nnb, L.cap), tile, &B.st->error);
+    const bool tiled = LS && stage_list(B.list, L.ld, i0, width, min(st->max_nnb, L.cap), tile, &B.st->error, L.wait_ns);
     const int i = i0 + threadIdx.x / TPA, l = threadIdx.x % TPA;
     const bool active = i < L.n;
     const int ti = (MULTI && active) ? B.type[s][i] : 0;

@@ -8,10 +8,11 @@
 // bitwise equal; energy sums differ in rounding only (other block partition).
 //
 // Grid barriers: all blocks are resident (cooperative launch); a barrier is
-// an arrival counter in device memory.  A wait gives up
-// after 1 s of %globaltimer, raises ERR_TIMEOUT and every later barrier of
-// the launch returns at once, so the kernel ends within about a second of a
-// stuck block and the host reports MD_ERR_TIMEOUT.
+// an arrival counter in device memory.  A wait gives up after the wait limit
+// (md_options.wait_limit_us, 1 s by default) of %globaltimer, raises
+// ERR_TIMEOUT and every later barrier of the launch returns at once, so the
+// kernel ends within about the limit of a stuck block and the host reports
+// MD_ERR_TIMEOUT.
 #include "pair_kernels.cuh"
 #include "rebuild_device.cuh"
 
@@ -44,7 +45,7 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 // (b + 1) x gridDim.x.  Arrival is a release add, the wait an acquire load, so
 // every block sees the writes all blocks made before the barrier.  Returns
 // false once any wait of the launch has timed out.
-__device__ __forceinline__ bool grid_barrier(PersistScratch *ps, unsigned *err)
+__device__ __forceinline__ bool grid_barrier(PersistScratch *ps, unsigned *err, uint64_t wait_ns)
 {
     __shared__ int ok;
     __syncthreads();
@@ -63,7 +64,7 @@ __device__ __forceinline__ bool grid_barrier(PersistScratch *ps, unsigned *err)
             if (a + 1 != target) {
                 const uint64_t t0 = global_ns();
                 while (ld_acquire(&ps->arrive) < target) {
-                    if ((ld_acquire(err) & ERR_TIMEOUT) || global_ns() - t0 > kWaitLimitNs) {
+                    if ((ld_acquire(err) & ERR_TIMEOUT) || global_ns() - t0 > wait_ns) {
                         atomicOr(err, ERR_TIMEOUT);
                         good = 0;
                         break;
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(256) k_steps(Bufs<R> B, Geom G, Launch L, long
         for (int i = gtid; i < n; i += nthreads) d2 = fmaxf(d2, open_atom<R>(B, L, s, sp, i));
         block_max_disp(d2, &ps->maxdisp[1]);
     }
-    if (!grid_barrier(ps, err)) return;
+    if (!grid_barrier(ps, err, L.wait_ns)) return;
 
     for (long long k = 0; k < nsteps; ++k) {
         const bool last = k == nsteps - 1;
@@ -122,25 +123,25 @@ __global__ void __launch_bounds__(256) k_steps(Bufs<R> B, Geom G, Launch L, long
 
         if (need) {
             for (int i = gtid; i < n; i += nthreads) bin_atom<R>(B, G, s, i);
-            if (!grid_barrier(ps, err)) return;
+            if (!grid_barrier(ps, err, L.wait_ns)) return;
             if (blockIdx.x == 0) scan_cells_block<R>(B, G.ncells);
-            if (!grid_barrier(ps, err)) return;
+            if (!grid_barrier(ps, err, L.wait_ns)) return;
             for (int i = gtid; i < n; i += nthreads) scatter_atom<R>(B, i);
-            if (!grid_barrier(ps, err)) return;
+            if (!grid_barrier(ps, err, L.wait_ns)) return;
             for (int c = gtid; c < G.ncells; c += nthreads) sort_cell<R>(B, s, c);
-            if (!grid_barrier(ps, err)) return;
+            if (!grid_barrier(ps, err, L.wait_ns)) return;
             for (int p = gtid; p < n; p += nthreads) permute_atom<R>(B, G, s, sp, p);
             if (gtid == 0) st->max_nnb = 0;
             s = 1 - s;
             since = 0;
             rebuilds += 1;
-            if (!grid_barrier(ps, err)) return;
+            if (!grid_barrier(ps, err, L.wait_ns)) return;
             for (int base = blockIdx.x * blockDim.x; base < n; base += nthreads) {
                 const int p = base + threadIdx.x;
                 const int cnt = (p < n) ? list_atom<R>(B, G, s, sp, p, L.ld, L.cap) : 0;
                 block_max_nnb(cnt, &st->max_nnb);
             }
-            if (!grid_barrier(ps, err)) return;
+            if (!grid_barrier(ps, err, L.wait_ns)) return;
         }
 
         // density pass
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(256) k_steps(Bufs<R> B, Geom G, Launch L, long
                 block_sums_t<1, R>(v, B.partials, L.pstride, 0);
             }
         }
-        if (!grid_barrier(ps, err)) return;
+        if (!grid_barrier(ps, err, L.wait_ns)) return;
 
         // force pass with the closing kick (and, but for the last step, the
         // next opening kick and the drift)
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(256) k_steps(Bufs<R> B, Geom G, Launch L, long
                 block_max_disp(d2max, &ps->maxdisp[k & 1]);
             }
         }
-        if (!grid_barrier(ps, err)) return;
+        if (!grid_barrier(ps, err, L.wait_ns)) return;
     }
 
     // energies of the last step, counters back to DevState

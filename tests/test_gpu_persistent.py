@@ -117,3 +117,20 @@ def test_single_launch_after_set_state_and_auto_threshold():
     big = I.bcc_cube(33)  # 71,874 atoms: above the automatic threshold
     with binding.MD(big, precision="mixed") as md:
         assert md.stats()["persistent_blocks"] == 0
+
+
+def test_wait_limit_raises_timeout_and_the_context_recovers():
+    """A grid-barrier wait longer than the configured limit (1 us here, so the
+    barriers of the single launch run out) ends the launch with
+    MD_ERR_TIMEOUT; md_set_state clears it and the context answers again."""
+    s = I.bcc_2000_fp64()
+    with binding.MD(s, precision="mixed", persistent="on", lanes_per_atom=2, wait_limit_us=1) as md:
+        md.step(200, 2.0)
+        with pytest.raises(binding.MDError) as e:
+            md.sync()
+        assert e.value.status == -6  # MD_ERR_TIMEOUT
+        md.set_state(s.pos, s.vel, 0)
+        assert rel(md.forces(), oracle_forces(s, s.pos)) < TOL["mixed"]
+    with pytest.raises(binding.MDError) as e:
+        binding.MD(s, wait_limit_us=-1)
+    assert e.value.status == -1
