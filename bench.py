@@ -373,6 +373,74 @@ def run_adjoint(args):
                       "gradient_vs_central_fd_rel_err_12_knots": err}), flush=True)
 
 
+def run_model(args):
+    """GB300 counterpart of the paper's linear time model (Eq. 6), which
+    writes the time of a timestep as a cost per candidate, a cost per
+    interaction and a fixed cost.  The 799,496-atom BCC system is evaluated
+    at dt = 0 (nothing moves) for cutoffs and skins that vary the list length
+    n_list (entries per atom, within r_cut + skin) and the interactions
+    n_inter (within r_cut) independently; the list is rebuilt every step so
+    that each evaluation also times a build over n_cand = 27 cells' atoms.
+    Least-squares fits, in ns per atom:
+      density + force = a n_list + b n_inter + c
+      list build      = a' n_cand + b' n_list + c'."""
+    import dataclasses
+
+    import numpy as np
+    import torch
+    from paper_2405_07898_gb300 import binding, inputs as I
+
+    torch.cuda.set_device(0)
+    grid = [(3.5, 0.3), (3.5, 0.8), (3.5, 1.4), (4.5, 0.3), (4.5, 0.7), (4.5, 1.1), (5.0, 0.3), (5.0, 0.9),
+            (5.6, 0.3), (5.6, 0.9), (6.2, 0.3), (6.2, 0.9)]
+    rng = np.random.default_rng(7898)
+    rows = []
+    for r_cut, skin in grid:
+        p = dataclasses.replace(I.BCC_TA_LIKE, r_cut=r_cut, skin=skin)
+        s = I.thermal_system(p, (74, 74, 73), 0.02, 300.0, I.SEED_BASE + 1, label="bcc_799496")
+        with binding.MD(s, precision="mixed", persistent="off", rebuild_every=1) as md:
+            prof = md.profile(args.profile_steps, 0.0)
+            off, js = md.neighbors()
+            pos, _, _ = md.get_state()
+            nc, _, _ = md.cells()
+        n = s.n
+        n_list = off[-1] / n
+        sample = rng.choice(n, size=4000, replace=False)
+        inter = 0
+        for i in sample:
+            d = pos[js[off[i]:off[i + 1]]] - pos[i]
+            d -= s.box * np.round(d / s.box)
+            inter += int(((d * d).sum(1) < r_cut * r_cut).sum())
+        n_inter = inter / len(sample)
+        n_cand = 27.0 * n / float(np.prod(nc.astype(np.float64)))
+        rows.append({"r_cut": r_cut, "skin": skin, "n_list": n_list, "n_inter": n_inter, "n_cand": n_cand,
+                     "pair_ns_per_atom": 1e6 * (prof["density_ms"] + prof["force_ms"]) / n,
+                     "density_ns_per_atom": 1e6 * prof["density_ms"] / n,
+                     "force_ns_per_atom": 1e6 * prof["force_ms"] / n,
+                     "build_ns_per_atom": 1e6 * prof["rebuild_ms"] / n})
+    A = np.array([[r["n_list"], r["n_inter"], 1.0] for r in rows])
+    Ab = np.array([[r["n_cand"], r["n_list"], 1.0] for r in rows])
+
+    def fit(M, key):
+        y = np.array([r[key] for r in rows])
+        c, *_ = np.linalg.lstsq(M, y, rcond=None)
+        pred = M @ c
+        r2 = 1.0 - float(((y - pred) ** 2).sum() / ((y - y.mean()) ** 2).sum())
+        return [float(v) for v in c], r2
+
+    (a, b, c), r2 = fit(A, "pair_ns_per_atom")
+    (ad, bd, cd), r2d = fit(A, "density_ns_per_atom")
+    (af, bf, cf), r2f = fit(A, "force_ns_per_atom")
+    (ab, bb, cb), r2b = fit(Ab, "build_ns_per_atom")
+    print(json.dumps({"workload": "linear_time_model_bcc_799496_mixed", "unit": "ns per atom",
+                      "points": rows,
+                      "pair_passes": {"per_list_entry": a, "per_interaction": b, "fixed": c, "r2": r2},
+                      "density": {"per_list_entry": ad, "per_interaction": bd, "fixed": cd, "r2": r2d},
+                      "force": {"per_list_entry": af, "per_interaction": bf, "fixed": cf, "r2": r2f},
+                      "list_build": {"per_candidate": ab, "per_list_entry": bb, "fixed": cb, "r2": r2b}}),
+          flush=True)
+
+
 def run_drift(args):
     """NVE energy drift: the 250,000-atom Sigma-5 bicrystal at 1,000 K and the
     799,496-atom box at 300 K, mixed precision, dt = 2 fs; total energy
@@ -511,7 +579,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="bcc_799496", choices=["bcc_799496", "sweep", "drift", "batch", "adjoint"],
+    ap.add_argument("--workload", default="bcc_799496", choices=["bcc_799496", "sweep", "drift", "batch", "adjoint", "model"],
                     help="bcc_799496: the benchmark line; sweep / drift: the strong-scaling sweep and the "
                          "NVE drift runs (their own JSON lines)")
     ap.add_argument("--drift-steps", type=int, default=100000)
@@ -536,6 +604,8 @@ def main():
         run_batch(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
+    elif args.workload == "model":
+        run_model(args)
     else:
         run_ours(args)
 
