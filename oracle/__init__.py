@@ -61,19 +61,19 @@ def lib():
                                      C.POINTER(_Knots), C.c_double, C.c_double]
         L.orc_pot_create.restype = C.c_void_p
         L.orc_pot_destroy.argtypes = [C.c_void_p]
-        L.orc_wrap.argtypes = [C.c_int64, _dp, _dp]
-        L.orc_cell_dims.argtypes = [_dp, C.c_double, _ip]
+        L.orc_wrap.argtypes = [C.c_int64, _dp, C.c_int, _dp]
+        L.orc_cell_dims.argtypes = [_dp, C.c_int, C.c_double, _ip]
         L.orc_cell_dims.restype = C.c_int
-        L.orc_cells.argtypes = [C.c_int64, _dp, C.c_double, _dp, _ip, _ip]
+        L.orc_cells.argtypes = [C.c_int64, _dp, C.c_int, C.c_double, _dp, _ip, _ip]
         L.orc_cells.restype = C.c_int
         for name in ("orc_list_cells", "orc_list_brute"):
             fn = getattr(L, name)
-            fn.argtypes = [C.c_int64, _dp, C.c_double, _dp, _lp, _ip, C.c_int64]
+            fn.argtypes = [C.c_int64, _dp, C.c_int, C.c_double, _dp, _lp, _ip, C.c_int64]
             fn.restype = C.c_int64
-        L.orc_eam_eval.argtypes = [C.c_void_p, C.c_int64, _dp, _dp, _ip, _lp, _ip, _dp, _dp, _dp,
+        L.orc_eam_eval.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int, _dp, _ip, _lp, _ip, _dp, _dp, _dp,
                                    _dp, _dp]
         L.orc_eam_eval.restype = C.c_int
-        L.orc_sys_create.argtypes = [C.c_void_p, C.c_int64, _dp, _dp, _dp, _ip]
+        L.orc_sys_create.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int, _dp, _dp, _ip]
         L.orc_sys_create.restype = C.c_void_p
         L.orc_sys_destroy.argtypes = [C.c_void_p]
         L.orc_sys_step.argtypes = [C.c_void_p, C.c_int64, C.c_double, C.c_int32]
@@ -83,8 +83,8 @@ def lib():
         L.orc_sys_get.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, _dp, _lp]
         L.orc_spline_basis.argtypes = [C.c_int32, C.c_double, C.c_int32, C.c_int32, _dp]
         L.orc_spline_basis.restype = C.c_int
-        L.orc_force_match.argtypes = [C.c_void_p, C.c_int64, _dp, _dp, C.c_double, _dp, C.c_double, _dp,
-                                      _dp, _dp, _dp, _dp, _dp]
+        L.orc_force_match.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int, _dp, C.c_double, _dp, C.c_double,
+                                      _dp, _dp, _dp, _dp, _dp, _dp]
         L.orc_force_match.restype = C.c_int
         _lib = L
     return _lib
@@ -174,39 +174,42 @@ class Potential:
             self.handle = None
 
 
-def wrap(pos, box):
+# `open_axes`: one bit per open (non-periodic) axis, 1: x, 2: y, 4: z.
+
+
+def wrap(pos, box, open_axes: int = 0):
     out = _f64(pos).copy()
-    lib().orc_wrap(out.shape[0], _d(_f64(box)), _d(out))
+    lib().orc_wrap(out.shape[0], _d(_f64(box)), int(open_axes), _d(out))
     return out
 
 
-def cell_dims(box, r_list):
+def cell_dims(box, r_list, open_axes: int = 0):
     nc = np.zeros(3, dtype=np.int32)
-    if lib().orc_cell_dims(_d(_f64(box)), r_list, _i(nc)):
-        raise ValueError("box shorter than 3 r_list along some axis")
+    if lib().orc_cell_dims(_d(_f64(box)), int(open_axes), r_list, _i(nc)):
+        raise ValueError("box shorter than 3 r_list along a periodic axis (r_list along an open one)")
     return nc
 
 
-def cells(pos, box, r_list):
+def cells(pos, box, r_list, open_axes: int = 0):
     """(ncell, cell_start, cell_atoms) for wrapped positions."""
-    nc = cell_dims(box, r_list)
+    nc = cell_dims(box, r_list, open_axes)
     ncells = int(np.prod(nc.astype(np.int64)))
     start = np.zeros(ncells + 1, dtype=np.int32)
     atoms = np.zeros(max(pos.shape[0], 1), dtype=np.int32)
     pos = _f64(pos)
-    if lib().orc_cells(pos.shape[0], _d(_f64(box)), r_list, _d(pos), _i(start), _i(atoms)):
+    if lib().orc_cells(pos.shape[0], _d(_f64(box)), int(open_axes), r_list, _d(pos), _i(start), _i(atoms)):
         raise ValueError("cells failed")
     return nc, start, atoms[: pos.shape[0]]
 
 
-def _list(fn, pos, box, r_list):
+def _list(fn, pos, box, r_list, open_axes):
     pos = _f64(pos)
     n = pos.shape[0]
     off = np.zeros(n + 1, dtype=np.int64)
     cap = max(64 * n, 1)
     while True:
         js = np.zeros(cap, dtype=np.int32)
-        m = fn(n, _d(_f64(box)), r_list, _d(pos), _l(off), _i(js), cap)
+        m = fn(n, _d(_f64(box)), int(open_axes), r_list, _d(pos), _l(off), _i(js), cap)
         if m < 0:
             raise ValueError("neighbour list failed")
         if m <= cap:
@@ -214,23 +217,23 @@ def _list(fn, pos, box, r_list):
         cap = int(m)
 
 
-def neighbors_cells(pos, box, r_list):
+def neighbors_cells(pos, box, r_list, open_axes: int = 0):
     """CSR neighbour list from the 27-cell stencil (positions wrapped)."""
-    return _list(lib().orc_list_cells, pos, box, r_list)
+    return _list(lib().orc_list_cells, pos, box, r_list, open_axes)
 
 
-def neighbors_brute(pos, box, r_list):
+def neighbors_brute(pos, box, r_list, open_axes: int = 0):
     """CSR neighbour list by testing all pairs."""
-    return _list(lib().orc_list_brute, pos, box, r_list)
+    return _list(lib().orc_list_brute, pos, box, r_list, open_axes)
 
 
-def eam_eval(pot: Potential, pos, box, types, off=None, js=None):
+def eam_eval(pot: Potential, pos, box, types, off=None, js=None, open_axes: int = 0):
     """rho, F', forces, (E_embed, E_pair), virial (xx,yy,zz,xy,xz,yz) at pos."""
     pos = _f64(pos)
     n = pos.shape[0]
     types = np.ascontiguousarray(types, dtype=np.int32)
     if off is None:
-        off, js = neighbors_cells(wrap(pos, box), box, pot.r_list)
+        off, js = neighbors_cells(wrap(pos, box, open_axes), box, pot.r_list, open_axes)
     rho = np.zeros(n)
     Fp = np.zeros(n)
     force = np.zeros((n, 3))
@@ -238,23 +241,24 @@ def eam_eval(pot: Potential, pos, box, types, off=None, js=None):
     virial = np.zeros(6)
     js = np.ascontiguousarray(js, dtype=np.int32)
     off = np.ascontiguousarray(off, dtype=np.int64)
-    lib().orc_eam_eval(pot.handle, n, _d(_f64(box)), _d(pos), _i(types), _l(off), _i(js),
+    lib().orc_eam_eval(pot.handle, n, _d(_f64(box)), int(open_axes), _d(pos), _i(types), _l(off), _i(js),
                        _d(rho), _d(Fp), _d(force), _d(energy), _d(virial))
     return rho, Fp, force, energy, virial
 
 
 class System:
-    """Serial FP64 molecular dynamics of one periodic system."""
+    """Serial FP64 molecular dynamics of one system (periodic, or open along
+    the axes of `open_axes`)."""
 
-    def __init__(self, pot: Potential, box, pos, vel, types):
+    def __init__(self, pot: Potential, box, pos, vel, types, open_axes: int = 0):
         self.pot = pot
         self.n = int(pos.shape[0])
         self._box = _f64(box)
         pos = _f64(pos)
         vel = _f64(vel) if vel is not None else np.zeros_like(pos)
         types = np.ascontiguousarray(types, dtype=np.int32)
-        self.handle = lib().orc_sys_create(pot.handle, self.n, _d(self._box), _d(pos), _d(vel),
-                                           _i(types))
+        self.handle = lib().orc_sys_create(pot.handle, self.n, _d(self._box), int(open_axes), _d(pos),
+                                           _d(vel), _i(types))
         if not self.handle:
             raise ValueError("oracle system create failed (box < 3 r_list?)")
 
@@ -304,7 +308,7 @@ def spline_basis(knots) -> np.ndarray:
     return M
 
 
-def force_match(pot: Potential, pos, box, e_ref: float, f_ref, w: float):
+def force_match(pot: Potential, pos, box, e_ref: float, f_ref, w: float, open_axes: int = 0):
     """Loss (E - E_ref)^2/N + w sum |F - F_ref|^2 of one single-type
     configuration and dL/d(coefficients) of phi, f, F (each (n-1, 4)); also
     returns E and F."""
@@ -317,7 +321,8 @@ def force_match(pot: Potential, pos, box, e_ref: float, f_ref, w: float):
     loss = C.c_double()
     e = C.c_double()
     force = np.zeros((n, 3))
-    rc = lib().orc_force_match(pot.handle, n, _d(_f64(box)), _d(pos), float(e_ref), _d(_f64(f_ref)),
+    rc = lib().orc_force_match(pot.handle, n, _d(_f64(box)), int(open_axes), _d(pos), float(e_ref),
+                               _d(_f64(f_ref)),
                                float(w), C.byref(loss), _d(g_phi), _d(g_f), _d(g_F), C.byref(e),
                                _d(force))
     if rc:

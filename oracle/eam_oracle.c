@@ -217,49 +217,61 @@ void orc_pot_destroy(orc_pot *p)
 }
 
 /* ------------------------------------------------------------------------ */
-/* periodic geometry (Section "Periodic Boundary Conditions")               */
+/* geometry: periodic axes (Section "Periodic Boundary Conditions") and open */
+/* axes (the open, non-periodic boundaries of the thin-slab workloads,       */
+/* Section "How Performance Was Measured").  `open` holds one bit per axis   */
+/* (1: x, 2: y, 4: z) that is open; on an open axis the box is the extent of */
+/* the cell grid, positions are not wrapped and displacements are plain      */
+/* differences.                                                              */
 
-/* x <- x - L floor(x / L), per coordinate. */
-void orc_wrap(int64_t n, const double box[3], double *pos)
+static int is_open(int open, int d) { return (open >> d) & 1; }
+
+/* x <- x - L floor(x / L), per coordinate of the periodic axes. */
+void orc_wrap(int64_t n, const double box[3], int open, double *pos)
 {
     for (int64_t i = 0; i < n; ++i)
         for (int d = 0; d < 3; ++d) {
+            if (is_open(open, d)) continue;
             double x = pos[3 * i + d];
             double q = floor(x / box[d]);
             pos[3 * i + d] = x - box[d] * q;
         }
 }
 
-/* Minimum-image displacement x_j - x_i along one axis (|raw| < 1.5 L). */
-static double min_image(double xj, double xi, double L)
+/* Displacement x_j - x_i along one axis: the minimum image on a periodic
+ * axis (|raw| < 1.5 L), the difference on an open one. */
+static double min_image(double xj, double xi, double L, int open_axis)
 {
     double d = xj - xi;
+    if (open_axis) return d;
     if (d > 0.5 * L) d = d - L;
     else if (d < -0.5 * L) d = d + L;
     return d;
 }
 
 /* Squared distance, summed in the fixed order (dx^2 + dy^2) + dz^2. */
-static double dist2(const double *xi, const double *xj, const double box[3], double d[3])
+static double dist2(const double *xi, const double *xj, const double box[3], int open, double d[3])
 {
-    d[0] = min_image(xj[0], xi[0], box[0]);
-    d[1] = min_image(xj[1], xi[1], box[1]);
-    d[2] = min_image(xj[2], xi[2], box[2]);
+    d[0] = min_image(xj[0], xi[0], box[0], is_open(open, 0));
+    d[1] = min_image(xj[1], xi[1], box[1], is_open(open, 1));
+    d[2] = min_image(xj[2], xi[2], box[2], is_open(open, 2));
     return (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
 }
 
-/* Cells per axis n_d = floor(L_d / r_list); the method needs n_d >= 3. */
-int orc_cell_dims(const double box[3], double r_list, int32_t ncell[3])
+/* Cells per axis n_d = floor(L_d / r_list); a periodic axis needs n_d >= 3
+ * (the 27-cell stencil may not meet its own image), an open axis n_d >= 1. */
+int orc_cell_dims(const double box[3], int open, double r_list, int32_t ncell[3])
 {
     for (int d = 0; d < 3; ++d) {
         double q = floor(box[d] / r_list);
         ncell[d] = (int32_t)q;
-        if (ncell[d] < 3) return -1;
+        if (ncell[d] < (is_open(open, d) ? 1 : 3)) return -1;
     }
     return 0;
 }
 
-/* Cell of a wrapped position: c_d = min(floor(x_d * (n_d / L_d)), n_d - 1). */
+/* Cell of a position: c_d = floor(x_d * (n_d / L_d)) clamped to [0, n_d - 1]
+ * (on an open axis, atoms outside the box go to the edge cells). */
 static int64_t cell_of(const double *x, const double box[3], const int32_t ncell[3])
 {
     int64_t c[3];
@@ -276,11 +288,11 @@ static int64_t cell_of(const double *x, const double box[3], const int32_t ncell
 
 /* Stable counting sort of atoms into cells: cell_start[c] .. cell_start[c+1]
  * index cell_atoms, which lists the atoms of cell c in ascending index. */
-int orc_cells(int64_t n, const double box[3], double r_list, const double *pos,
+int orc_cells(int64_t n, const double box[3], int open, double r_list, const double *pos,
               int32_t *cell_start, int32_t *cell_atoms)
 {
     int32_t nc[3];
-    if (orc_cell_dims(box, r_list, nc)) return -1;
+    if (orc_cell_dims(box, open, r_list, nc)) return -1;
     int64_t ncells = (int64_t)nc[0] * nc[1] * nc[2];
     int64_t *cursor = calloc((size_t)ncells, sizeof(int64_t));
     int64_t *cell = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
@@ -302,20 +314,20 @@ int orc_cells(int64_t n, const double box[3], double r_list, const double *pos,
 }
 
 /* Neighbour list (Section "Neighbor list"): for each atom, the atoms j != i
- * of the 27 surrounding cells whose squared minimum-image distance is below
- * r_list^2.  CSR output: offsets[n+1], js[offsets[i] .. offsets[i+1]).
+ * of the 27 surrounding cells (cells beyond an open edge do not exist) whose
+ * squared minimum-image distance is below r_list^2.  CSR output: offsets[n+1], js[offsets[i] .. offsets[i+1]).
  * Returns the total number of entries (which may exceed cap: then only the
  * count is meaningful), or a negative error code. */
-int64_t orc_list_cells(int64_t n, const double box[3], double r_list, const double *pos,
+int64_t orc_list_cells(int64_t n, const double box[3], int open, double r_list, const double *pos,
                        int64_t *offsets, int32_t *js, int64_t cap)
 {
     int32_t nc[3];
-    if (orc_cell_dims(box, r_list, nc)) return -1;
+    if (orc_cell_dims(box, open, r_list, nc)) return -1;
     int64_t ncells = (int64_t)nc[0] * nc[1] * nc[2];
     int32_t *start = malloc(sizeof(int32_t) * (size_t)(ncells + 1));
     int32_t *atoms = malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     if (!start || !atoms) { free(start); free(atoms); return -2; }
-    orc_cells(n, box, r_list, pos, start, atoms);
+    orc_cells(n, box, open, r_list, pos, start, atoms);
     double rl2 = r_list * r_list;
     int64_t m = 0;
     for (int64_t i = 0; i < n; ++i) {
@@ -326,15 +338,19 @@ int64_t orc_list_cells(int64_t n, const double box[3], double r_list, const doub
         for (int dz = -1; dz <= 1; ++dz)
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
-                    int64_t ex = (cx + dx + nc[0]) % nc[0];
-                    int64_t ey = (cy + dy + nc[1]) % nc[1];
-                    int64_t ez = (cz + dz + nc[2]) % nc[2];
+                    int64_t ex = cx + dx, ey = cy + dy, ez = cz + dz;
+                    if ((ex < 0 || ex >= nc[0]) && is_open(open, 0)) continue;
+                    if ((ey < 0 || ey >= nc[1]) && is_open(open, 1)) continue;
+                    if ((ez < 0 || ez >= nc[2]) && is_open(open, 2)) continue;
+                    ex = (ex + nc[0]) % nc[0];
+                    ey = (ey + nc[1]) % nc[1];
+                    ez = (ez + nc[2]) % nc[2];
                     int64_t e = (ez * nc[1] + ey) * nc[0] + ex;
                     for (int32_t q = start[e]; q < start[e + 1]; ++q) {
                         int32_t j = atoms[q];
                         if (j == i) continue;
                         double d[3];
-                        if (dist2(xi, pos + 3 * (int64_t)j, box, d) < rl2) {
+                        if (dist2(xi, pos + 3 * (int64_t)j, box, open, d) < rl2) {
                             if (m < cap) js[m] = j;
                             m += 1;
                         }
@@ -348,7 +364,7 @@ int64_t orc_list_cells(int64_t n, const double box[3], double r_list, const doub
 }
 
 /* The same list by testing every pair (the definition, O(N^2)). */
-int64_t orc_list_brute(int64_t n, const double box[3], double r_list, const double *pos,
+int64_t orc_list_brute(int64_t n, const double box[3], int open, double r_list, const double *pos,
                        int64_t *offsets, int32_t *js, int64_t cap)
 {
     double rl2 = r_list * r_list;
@@ -358,7 +374,7 @@ int64_t orc_list_brute(int64_t n, const double box[3], double r_list, const doub
         for (int64_t j = 0; j < n; ++j) {
             if (j == i) continue;
             double d[3];
-            if (dist2(pos + 3 * i, pos + 3 * j, box, d) < rl2) {
+            if (dist2(pos + 3 * i, pos + 3 * j, box, open, d) < rl2) {
                 if (m < cap) js[m] = (int32_t)j;
                 m += 1;
             }
@@ -373,7 +389,7 @@ int64_t orc_list_brute(int64_t n, const double box[3], double r_list, const doub
 
 /* Electron density at atom i (Eq. 2, j != i, r < r_cut), the embedding
  * derivative F'_i(rho_i), and the embedding energy sum of Eq. 3. */
-static double density_pass(const orc_pot *p, int64_t n, const double box[3], const double *pos,
+static double density_pass(const orc_pot *p, int64_t n, const double box[3], int open, const double *pos,
                            const int32_t *types, const int64_t *off, const int32_t *js,
                            double *rho, double *Fp)
 {
@@ -384,7 +400,7 @@ static double density_pass(const orc_pot *p, int64_t n, const double box[3], con
         for (int64_t q = off[i]; q < off[i + 1]; ++q) {
             int64_t j = js[q];
             double d[3];
-            double r2 = dist2(pos + 3 * i, pos + 3 * j, box, d);
+            double r2 = dist2(pos + 3 * i, pos + 3 * j, box, open, d);
             if (r2 < rc2) r_i += spl(&p->f[types[j]], sqrt(r2), NULL, NULL);
         }
         double dF;
@@ -402,7 +418,7 @@ static double density_pass(const orc_pot *p, int64_t n, const double box[3], con
  * the pair energy (1/2) sum_{i != j} phi_ij(r_ij)               (Eq. 3),
  * and the virial W_ab = -(1/2) sum_i sum_j s_ij d_a d_b / r, stored
  * xx, yy, zz, xy, xz, yz. */
-static double force_pass(const orc_pot *p, int64_t n, const double box[3], const double *pos,
+static double force_pass(const orc_pot *p, int64_t n, const double box[3], int open, const double *pos,
                          const int32_t *types, const int64_t *off, const int32_t *js,
                          const double *Fp, double *force, double virial[6])
 {
@@ -416,7 +432,7 @@ static double force_pass(const orc_pot *p, int64_t n, const double box[3], const
             int64_t j = js[q];
             int32_t tj = types[j];
             double d[3];
-            double r2 = dist2(pos + 3 * i, pos + 3 * j, box, d);
+            double r2 = dist2(pos + 3 * i, pos + 3 * j, box, open, d);
             if (!(r2 < rc2)) continue;
             double r = sqrt(r2);
             double dphi, dfj, dfi;
@@ -441,7 +457,7 @@ static double force_pass(const orc_pot *p, int64_t n, const double box[3], const
 /* Density, forces, energies and virial for positions `pos` and a
  * neighbour list built for them (or for positions within skin/2 of them).
  * Any output pointer may be NULL except force. */
-int orc_eam_eval(const orc_pot *p, int64_t n, const double box[3], const double *pos,
+int orc_eam_eval(const orc_pot *p, int64_t n, const double box[3], int open, const double *pos,
                  const int32_t *types, const int64_t *off, const int32_t *js,
                  double *rho, double *Fp, double *force, double energy[2], double virial[6])
 {
@@ -449,8 +465,8 @@ int orc_eam_eval(const orc_pot *p, int64_t n, const double box[3], const double 
     double *Fp_w = Fp ? Fp : malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double vir_w[6];
     if (!rho_w || !Fp_w) return -2;
-    double e_embed = density_pass(p, n, box, pos, types, off, js, rho_w, Fp_w);
-    double e_pair = force_pass(p, n, box, pos, types, off, js, Fp_w, force, vir_w);
+    double e_embed = density_pass(p, n, box, open, pos, types, off, js, rho_w, Fp_w);
+    double e_pair = force_pass(p, n, box, open, pos, types, off, js, Fp_w, force, vir_w);
     if (energy) { energy[0] = e_embed; energy[1] = e_pair; }
     if (virial) memcpy(virial, vir_w, sizeof(vir_w));
     if (!rho) free(rho_w);
@@ -465,6 +481,7 @@ typedef struct {
     const orc_pot *pot;
     int64_t n;
     double box[3];
+    int open;
     double *pos, *vel, *force, *rho, *Fp, *x_ref;
     int32_t *types;
     int64_t *off;
@@ -480,9 +497,9 @@ void orc_sys_destroy(orc_sys *s);
 static int rebuild(orc_sys *s)
 {
     double r_list = s->pot->r_cut + s->pot->skin;
-    orc_wrap(s->n, s->box, s->pos);
+    orc_wrap(s->n, s->box, s->open, s->pos);
     for (;;) {
-        int64_t m = orc_list_cells(s->n, s->box, r_list, s->pos, s->off, s->js, s->cap);
+        int64_t m = orc_list_cells(s->n, s->box, s->open, r_list, s->pos, s->off, s->js, s->cap);
         if (m < 0) return (int)m;
         if (m <= s->cap) break;
         free(s->js);
@@ -498,11 +515,11 @@ static int rebuild(orc_sys *s)
 
 static int evaluate(orc_sys *s)
 {
-    return orc_eam_eval(s->pot, s->n, s->box, s->pos, s->types, s->off, s->js, s->rho, s->Fp,
+    return orc_eam_eval(s->pot, s->n, s->box, s->open, s->pos, s->types, s->off, s->js, s->rho, s->Fp,
                         s->force, s->energy, s->virial);
 }
 
-orc_sys *orc_sys_create(const orc_pot *pot, int64_t n, const double box[3], const double *pos,
+orc_sys *orc_sys_create(const orc_pot *pot, int64_t n, const double box[3], int open, const double *pos,
                         const double *vel, const int32_t *types)
 {
     orc_sys *s = calloc(1, sizeof(orc_sys));
@@ -510,6 +527,7 @@ orc_sys *orc_sys_create(const orc_pot *pot, int64_t n, const double box[3], cons
     size_t nn = (size_t)(n > 0 ? n : 1);
     s->pot = pot;
     s->n = n;
+    s->open = open;
     memcpy(s->box, box, sizeof(s->box));
     s->pos = malloc(sizeof(double) * 3 * nn);
     s->vel = calloc(3 * nn, sizeof(double));
@@ -695,7 +713,7 @@ int orc_spline_basis(int32_t n, double h, int32_t bc_lo, int32_t bc_hi, double *
 /* Loss of one configuration and dL/d(coefficients) of phi, f and F (arrays
  * of 4(n-1) each, accumulated into: the caller zeroes them).  Returns the
  * energy and forces through e_out / f_out when given. */
-int orc_force_match(const orc_pot *p, int64_t n, const double box[3], const double *pos,
+int orc_force_match(const orc_pot *p, int64_t n, const double box[3], int open, const double *pos,
                     double e_ref, const double *f_ref, double w, double *loss,
                     double *g_phi, double *g_f, double *g_F, double *e_out, double *f_out)
 {
@@ -711,11 +729,11 @@ int orc_force_match(const orc_pot *p, int64_t n, const double box[3], const doub
     int32_t *js = malloc(sizeof(int32_t) * (size_t)cap);
     if (!wp || !types || !off || !rho || !Fp || !force || !g || !drho || !js) return -2;
     memcpy(wp, pos, sizeof(double) * 3 * (size_t)n);
-    orc_wrap(n, box, wp);
-    int64_t m = orc_list_cells(n, box, p->r_cut + p->skin, wp, off, js, cap);
+    orc_wrap(n, box, open, wp);
+    int64_t m = orc_list_cells(n, box, open, p->r_cut + p->skin, wp, off, js, cap);
     if (m < 0 || m > cap) return -3;
     double energy[2], vir[6];
-    orc_eam_eval(p, n, box, wp, types, off, js, rho, Fp, force, energy, vir);
+    orc_eam_eval(p, n, box, open, wp, types, off, js, rho, Fp, force, energy, vir);
     double E = energy[0] + energy[1];
     double A = 2.0 * (E - e_ref) / (double)n;
     double sq = 0.0;
@@ -731,7 +749,7 @@ int orc_force_match(const orc_pot *p, int64_t n, const double box[3], const doub
         for (int64_t q = off[i]; q < off[i + 1]; ++q) {
             int64_t j = js[q];
             double d[3];
-            double r2 = dist2(wp + 3 * i, wp + 3 * j, box, d);
+            double r2 = dist2(wp + 3 * i, wp + 3 * j, box, open, d);
             if (!(r2 < rc2)) continue;
             double r = sqrt(r2), df;
             spl(sf, r, &df, NULL);
@@ -750,7 +768,7 @@ int orc_force_match(const orc_pot *p, int64_t n, const double box[3], const doub
         for (int64_t q = off[i]; q < off[i + 1]; ++q) {
             int64_t j = js[q];
             double d[3];
-            double r2 = dist2(wp + 3 * i, wp + 3 * j, box, d);
+            double r2 = dist2(wp + 3 * i, wp + 3 * j, box, open, d);
             if (!(r2 < rc2)) continue;
             double r = sqrt(r2);
             double dr = (d[0] * (g[3 * j] - g[3 * i]) + d[1] * (g[3 * j + 1] - g[3 * i + 1]) +

@@ -231,13 +231,15 @@ def maxwell(n: int, mass, temperature: float, rng: np.random.Generator):
 
 @dataclasses.dataclass
 class System:
-    """One periodic system: the inputs md_create takes."""
+    """One system: the inputs md_create takes.  open_axes has one bit per
+    open (non-periodic) axis, 1: x, 2: y, 4: z (0: fully periodic)."""
     box: np.ndarray
     pos: np.ndarray
     vel: np.ndarray
     types: np.ndarray
     pot: Potential
     label: str = ""
+    open_axes: int = 0
 
     @property
     def n(self) -> int:
@@ -253,6 +255,31 @@ def thermal_system(p: JohnsonParams, cells, sigma: float, temperature: float, se
     types = np.zeros(pos.shape[0], dtype=np.int32)
     return System(box=box, pos=pos, vel=vel, types=types, pot=johnson_potential(p, n_knots),
                   label=label or f"{p.lattice}{cells[0]}x{cells[1]}x{cells[2]}")
+
+
+def slab_system(p: JohnsonParams, cells, open_axes: int, vacuum: float, sigma: float, temperature: float,
+                seed: int, n_knots: int = 2000, label: str = "") -> System:
+    """A crystal with free surfaces on the open axes: the lattice of `cells`
+    unit cells, shifted by `vacuum` (Angstrom) along each open axis inside a
+    box that is the lattice extent plus 2 x vacuum there (the lattice period
+    along periodic axes); Gaussian displacements (not re-wrapped along open
+    axes) and Maxwell velocities."""
+    pos, box = lattice(p, *cells)
+    box = box.copy()
+    rng = np.random.Generator(np.random.PCG64(seed))
+    disp = rng.normal(0.0, sigma, size=pos.shape)
+    pos = pos + disp
+    for a in range(3):
+        if (open_axes >> a) & 1:
+            pos[:, a] += vacuum
+            box[a] += 2.0 * vacuum
+        else:
+            pos[:, a] = np.mod(pos[:, a], box[a])
+    vel = maxwell(pos.shape[0], p.mass, temperature, rng)
+    types = np.zeros(pos.shape[0], dtype=np.int32)
+    return System(box=box, pos=np.ascontiguousarray(pos), vel=vel, types=types, pot=johnson_potential(p, n_knots),
+                  label=label or f"{p.lattice}_slab{cells[0]}x{cells[1]}x{cells[2]}_open{open_axes}",
+                  open_axes=open_axes)
 
 
 # --------------------------------------------------------------------------
@@ -276,6 +303,21 @@ def bcc_799496() -> System:
 def bcc_cube(n: int, temperature: float = 300.0, sigma: float = 0.02, seed: int | None = None) -> System:
     return thermal_system(BCC_TA_LIKE, (n, n, n), sigma, temperature,
                           SEED_BASE + 100 + n if seed is None else seed, label=f"bcc_cube{n}")
+
+
+def ta_slab_801792() -> System:
+    """The size and shape of the paper's tantalum benchmark slab (Table
+    "Results for 800,000 atom models": 256 x 261 x 6 BCC unit cells, 801,792
+    atoms, open boundaries), with the BCC stand-in potential: all three axes
+    open, 6 A of vacuum on each side, sigma 0.02 A, 290 K."""
+    return slab_system(BCC_TA_LIKE, (256, 261, 6), 7, 6.0, 0.02, 290.0, SEED_BASE + 600, label="ta_slab_801792")
+
+
+def bcc_slab_small(open_axes: int = 4, seed: int = SEED_BASE + 601) -> System:
+    """2,160-atom BCC slab (12 x 10 x 9 cells) for parity tests: open along
+    the axes of open_axes with 5 A of vacuum, periodic along the others."""
+    return slab_system(BCC_TA_LIKE, (12, 10, 9), open_axes, 5.0, 0.03, 400.0, seed,
+                       label=f"bcc_slab_small_open{open_axes}")
 
 
 def multi_type_system(cells=(6, 6, 6), seed: int = SEED_BASE + 50, n_knots: int = 400) -> System:
