@@ -373,6 +373,30 @@ def run_adjoint(args):
                       "gradient_vs_central_fd_rel_err_12_knots": err}), flush=True)
 
 
+def run_slab(args):
+    """The paper's benchmark geometry: a 256 x 261 x 6 BCC-cell slab (801,792
+    atoms) with open boundaries on all axes and the BCC stand-in potential,
+    mixed precision, dt = 2 fs: timesteps/s of md_step (CUDA events on the
+    library's stream) and the per-kernel durations."""
+    import torch
+    from paper_2405_07898_gb300 import binding, inputs as I
+
+    torch.cuda.set_device(0)
+    s = I.ta_slab_801792()
+    with binding.MD(s, precision="mixed") as md:
+        md.step(50, DT_FS)
+        steps = 500
+        t = _timed_steps(md, steps, DT_FS)
+        prof = md.profile(args.profile_steps, DT_FS)
+        st = md.stats()
+    print(json.dumps({"workload": "ta_slab_801792_open_mixed", "metric": "timesteps/s", "value": steps / t,
+                      "unit": "timesteps/s", "atoms": s.n, "open_axes": s.open_axes, "steps": steps,
+                      "atom_steps_per_s": s.n * steps / t,
+                      "kernels_ms": {"density": prof["density_ms"], "force": prof["force_ms"],
+                                     "rebuild": prof["rebuild_ms"]},
+                      "max_neighbors": st["max_neighbors"], "rebuilds": st["rebuilds"]}), flush=True)
+
+
 def run_model(args):
     """GB300 counterpart of the paper's linear time model (Eq. 6), which
     writes the time of a timestep as a cost per candidate, a cost per
@@ -579,7 +603,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="bcc_799496", choices=["bcc_799496", "sweep", "drift", "batch", "adjoint", "model"],
+    ap.add_argument("--workload", default="bcc_799496", choices=["bcc_799496", "sweep", "drift", "batch", "adjoint", "model", "slab"],
                     help="bcc_799496: the benchmark line; sweep / drift: the strong-scaling sweep and the "
                          "NVE drift runs (their own JSON lines)")
     ap.add_argument("--drift-steps", type=int, default=100000)
@@ -606,6 +630,8 @@ def main():
         run_adjoint(args)
     elif args.workload == "model":
         run_model(args)
+    elif args.workload == "slab":
+        run_slab(args)
     else:
         run_ours(args)
 

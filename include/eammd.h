@@ -150,6 +150,17 @@ enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2, MD_SCH
  *                    lanes per atom; energy sums differ in rounding only.  A
  *                    grid-barrier wait longer than 1 s ends the launch and
  *                    raises MD_ERR_TIMEOUT.
+ *   open_axes        one bit per open (non-periodic) axis: 1 = x, 2 = y,
+ *                    4 = z; 0 = fully periodic.  The free-surface slabs of
+ *                    the paper's benchmarks (Section "How Performance Was
+ *                    Measured": open boundaries).  On an open axis the box is
+ *                    the extent of the cell grid (edge >= r_cut + skin,
+ *                    against 3 (r_cut + skin) on a periodic axis),
+ *                    positions are not wrapped, pair vectors are plain
+ *                    differences, and an atom outside the box is binned into
+ *                    the edge cell (its list stays complete; keep atoms
+ *                    inside the box for the FP32 accuracy bound of the mixed
+ *                    path).  Batches are periodic only.
  *   wait_limit_us    longest device-side wait (a grid barrier of the single
  *                    launch, the bulk-copy barrier of list tiles) before the
  *                    kernel gives up and raises MD_ERR_TIMEOUT; 0 = 1 s.
@@ -172,12 +183,14 @@ typedef struct {
     int32_t stage_capacity;
     int32_t persistent;
     int32_t wait_limit_us;
+    int32_t open_axes;
 } md_options;
 
 void md_options_default(md_options *opt);
 
-/* Create a system of n atoms in the periodic box [0,box[0]) x [0,box[1]) x
- * [0,box[2]).  pos: n*3 Angstrom (any image; wrapped on entry);
+/* Create a system of n atoms in the box [0,box[0]) x [0,box[1]) x
+ * [0,box[2]), periodic but along the axes of opt->open_axes.  pos: n*3
+ * Angstrom (any image along periodic axes: wrapped on entry);
  * vel: n*3 Angstrom/fs or NULL for zero; types: n values in [0, ntypes).
  * Builds the tables, bins the atoms, builds the list and evaluates the
  * forces, energies and virial of the initial state.  Synchronises.

@@ -58,7 +58,8 @@ class Options(C.Structure):
                 ("alloc_ctx", C.c_void_p), ("schedule", C.c_int32),
                 ("stage_capacity", C.c_int32),
                 ("persistent", C.c_int32),
-                ("wait_limit_us", C.c_int32)]
+                ("wait_limit_us", C.c_int32),
+                ("open_axes", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -241,6 +242,7 @@ class MD:
         opt.stage_capacity = stage_capacity
         opt.persistent = PERSIST[persistent]
         opt.wait_limit_us = wait_limit_us
+        opt.open_axes = int(getattr(system, "open_axes", 0))
         self._keep = []
         if use_torch is None:
             try:

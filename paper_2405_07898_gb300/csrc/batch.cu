@@ -750,6 +750,7 @@ md_status md_batch_create(int32_t nrep, const md_replica *reps, int32_t npot, co
     md_options_default(&o);
     if (opt) o = *opt;
     if (o.precision != MD_PRECISION_MIXED) return bad(MD_ERR_ARG, "batches run the mixed-precision path");
+    if (o.open_axes != 0) return bad(MD_ERR_ARG, "batch replicas are periodic (open_axes must be 0)");
     if ((o.alloc == nullptr) != (o.free == nullptr)) return bad(MD_ERR_ARG, "alloc and free go together");
     if (o.rebuild_every < 1) o.rebuild_every = 10;
     // potentials: one type each, f and phi on one grid (fused rows)

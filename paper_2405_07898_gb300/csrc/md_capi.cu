@@ -312,8 +312,12 @@ md_status load_and_measure(md_ctx *ctx, const double *pos, const double *vel, in
         rc = read_state(ctx);
         if (rc != MD_OK) return rc;
         const DevState &hs = *ctx->st_host;
-        if ((hs.error & ERR_LIST_OVERFLOW) && ctx->opt.list_capacity <= 0) {
-            int cap = ((hs.max_nnb + hs.max_nnb / 8 + 8) + 3) & ~3;
+        // automatic capacity: at least the longest list of this build with
+        // room to grow (a density estimate from the box undercounts slabs
+        // with vacuum)
+        const int want = ((hs.max_nnb + hs.max_nnb / 4 + 8) + 3) & ~3;
+        if (((hs.error & ERR_LIST_OVERFLOW) || want > ctx->L.cap) && ctx->opt.list_capacity <= 0) {
+            int cap = std::max(want, ((hs.max_nnb + hs.max_nnb / 8 + 8) + 3) & ~3);
             if (!grow_list<R>(ctx, cap)) return ctx->fail(MD_ERR_OOM, "cannot grow the neighbour list");
             // the state is already sorted; rebuild from it with the larger capacity
             DevState again = hs;
@@ -1108,9 +1112,14 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
         if (s.x0 > 0.0 || s.x0 + (s.n - 1) * s.dx < pot->r_cut)
             return bad(MD_ERR_ARG, "phi tables must cover [0, r_cut]");
     }
+    const int open_mask = opt ? opt->open_axes : 0;
+    if (open_mask < 0 || open_mask > 7) return bad(MD_ERR_ARG, "open_axes must be a mask of bits 1 (x), 2 (y), 4 (z)");
     for (int a = 0; a < 3; ++a) {
         if (!(box[a] > 0.0) || !std::isfinite(box[a])) return bad(MD_ERR_ARG, "box edges must be > 0");
-        if (std::floor(box[a] / r_list) < 3.0) return bad(MD_ERR_BOX, "box edge shorter than 3 (r_cut + skin)");
+        const bool open_axis = (open_mask >> a) & 1;
+        if (std::floor(box[a] / r_list) < (open_axis ? 1.0 : 3.0))
+            return bad(MD_ERR_BOX, open_axis ? "open box edge shorter than r_cut + skin"
+                                             : "periodic box edge shorter than 3 (r_cut + skin)");
     }
     for (int64_t i = 0; i < 3 * n; ++i) {
         if (!std::isfinite(pos[i]) || (vel && !std::isfinite(vel[i])))
@@ -1173,6 +1182,7 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
         hmax = std::max(hmax, G.h[a]);
     }
     G.ncells = G.ncell[0] * G.ncell[1] * G.ncell[2];
+    G.open_mask = o.open_axes;
     G.rl2 = r_list * r_list;
     G.rc2 = pot->r_cut * pot->r_cut;
     // rounding bound of the screened r^2 (cell-relative coordinates, |u| <= h)

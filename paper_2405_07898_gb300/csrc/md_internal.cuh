@@ -96,6 +96,7 @@ struct Geom {
     double screen_lo;    // candidates with r2 below this are in the list for sure
     double screen_hi;    // ... above this are out for sure; in between: exact FP64 test
     double rc2;          // r_cut^2
+    int open_mask;       // one bit per open (non-periodic) axis: 1 x, 2 y, 4 z
     // the same in FP32, so that FP32 kernels convert nothing on the FP64 pipe
     float h_f[3];
     float rc2_f;

@@ -517,12 +517,14 @@ __device__ __forceinline__ bool stage_rows(const Bufs<R> &B, const Geom &G, cons
     if (threadIdx.x < 9) {
         const int t = threadIdx.x;
         int ey = cy + t % 3 - 1, ez = cz + t / 3 - 1;
+        const bool gone = ((ey < 0 || ey >= ny) && ((G.open_mask >> 1) & 1)) ||
+                          ((ez < 0 || ez >= nz) && ((G.open_mask >> 2) & 1));
         ey += (ey < 0) ? ny : ((ey >= ny) ? -ny : 0);
         ez += (ez < 0) ? nz : ((ez >= nz) ? -nz : 0);
         const int r = ez * ny + ey;
         const int s0 = B.cell_start[r * nx], s1 = B.cell_start[(r + 1) * nx];
         rstart[t] = s0;
-        rcount[t] = s1 - s0;
+        rcount[t] = gone ? 0 : s1 - s0;  // no row beyond an open edge
     }
     __syncthreads();
     if (threadIdx.x == 0) {

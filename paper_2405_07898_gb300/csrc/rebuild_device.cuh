@@ -11,7 +11,8 @@ namespace eammd {
 namespace {
 
 // Wrap x = xr + d into [0, L) exactly as x - L floor(x / L) (for |x| < 2L the
-// branch form below gives the same bits), then bin: c_d = floor(x_d n_d/L_d).
+// branch form below gives the same bits) on periodic axes, then bin:
+// c_d = floor(x_d n_d/L_d) clamped to [0, n_d - 1].
 // The slot inside the cell is the arrival order (fixed by sort_cell).
 template <class R>
 __device__ __forceinline__ void bin_atom(const Bufs<R> &B, const Geom &G, int s, int i)
@@ -22,7 +23,8 @@ __device__ __forceinline__ void bin_atom(const Bufs<R> &B, const Geom &G, int s,
     for (int a = 0; a < 3; ++a) {
         double L = G.box[a];
         double x = __dadd_rn(B.xr[s][a][i], B.d[a][i]);
-        if (x >= 0.0 && x < L) {
+        if (((G.open_mask >> a) & 1) || (x >= 0.0 && x < L)) {
+            // open axis: not wrapped (outside the box, the edge cell takes it)
         } else if (x < 0.0 && x >= -L) {
             x = __dadd_rn(x, L);
         } else if (x >= L && x < 2.0 * L) {
@@ -131,15 +133,18 @@ __device__ __forceinline__ void permute_atom(const Bufs<R> &B, const Geom &G, in
 
 // Exact list test for a candidate near the list radius: the minimum-image
 // squared distance with the operations and rounding order of the definition
-// (d = x_j - x_i, +-L once, (dx^2 + dy^2) + dz^2, no fused operations).
+// (d = x_j - x_i, +-L once on periodic axes, (dx^2 + dy^2) + dz^2, no fused
+// operations).
 __device__ __forceinline__ bool exact_in_list(const double *const xr[3], int p, int q, const Geom &G)
 {
     double d[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         double x = __dsub_rn(xr[a][q], xr[a][p]);
-        if (x > G.half_box[a]) x = __dsub_rn(x, G.box[a]);
-        else if (x < -G.half_box[a]) x = __dadd_rn(x, G.box[a]);
+        if (!((G.open_mask >> a) & 1)) {
+            if (x > G.half_box[a]) x = __dsub_rn(x, G.box[a]);
+            else if (x < -G.half_box[a]) x = __dadd_rn(x, G.box[a]);
+        }
         d[a] = x;
     }
     double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
@@ -147,7 +152,8 @@ __device__ __forceinline__ bool exact_in_list(const double *const xr[3], int p, 
 }
 
 // Verlet list of atom p: the atoms of the 27 surrounding cells (in stencil
-// order, ascending id inside a cell) closer than r_list.  The test runs in R
+// order, ascending id inside a cell; cells beyond an open edge do not exist)
+// closer than r_list.  The test runs in R
 // on the cell-centred coordinates; candidates within the rounding margin of
 // r_list are decided by exact_in_list, so the list is bit-identical to the
 // FP64 definition.  The 9 rows of the stencil are unrolled; the 3 cells of a
@@ -168,19 +174,29 @@ __device__ __forceinline__ int list_atom(const Bufs<R> &B, const Geom &G, int s,
     const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
     const R4 up = sw[p];
     uint32_t *lp = B.list + p;
+    const bool open_x = G.open_mask & 1, open_y = (G.open_mask >> 1) & 1, open_z = (G.open_mask >> 2) & 1;
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz) {
         int ez = cz + dz;
-        ez += (ez < 0) ? nz : ((ez >= nz) ? -nz : 0);
+        if (ez < 0 || ez >= nz) {
+            if (open_z) continue;  // no cell beyond an open edge
+            ez += (ez < 0) ? nz : -nz;
+        }
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
             int ey = cy + dy;
-            ey += (ey < 0) ? ny : ((ey >= ny) ? -ny : 0);
+            if (ey < 0 || ey >= ny) {
+                if (open_y) continue;
+                ey += (ey < 0) ? ny : -ny;
+            }
             const int row = (ez * ny + ey) * nx;
 #pragma unroll 1
             for (int dx = -1; dx <= 1; ++dx) {
                 int ex = cx + dx;
-                ex += (ex < 0) ? nx : ((ex >= nx) ? -nx : 0);
+                if (ex < 0 || ex >= nx) {
+                    if (open_x) continue;
+                    ex += (ex < 0) ? nx : -nx;
+                }
                 const int e = row + ex;
                 const uint32_t code = list_entry(0u, dx, dy, dz);
                 const R ox = (R)dx * hx - up.x, oy = (R)dy * hy - up.y, oz = (R)dz * hz - up.z;
