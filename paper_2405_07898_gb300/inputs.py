@@ -313,6 +313,15 @@ def ta_slab_801792() -> System:
     return slab_system(BCC_TA_LIKE, (256, 261, 6), 7, 6.0, 0.02, 290.0, SEED_BASE + 600, label="ta_slab_801792")
 
 
+def cu_slab_801792() -> System:
+    """The size and shape of the paper's copper benchmark slab (Table "Results
+    for 800,000 atom models": 174 x 192 x 6 FCC unit cells, 801,792 atoms,
+    open boundaries), with the FCC stand-in potential (42 interactions per
+    atom): all three axes open, 6 A of vacuum on each side, sigma 0.02 A,
+    290 K."""
+    return slab_system(FCC_CU_LIKE, (174, 192, 6), 7, 6.0, 0.02, 290.0, SEED_BASE + 602, label="cu_slab_801792")
+
+
 def bcc_slab_small(open_axes: int = 4, seed: int = SEED_BASE + 601) -> System:
     """2,160-atom BCC slab (12 x 10 x 9 cells) for parity tests: open along
     the axes of open_axes with 5 A of vacuum, periodic along the others."""

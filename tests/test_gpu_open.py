@@ -128,3 +128,16 @@ def test_paper_size_ta_slab_forces():
         f10 = md.forces()
     _, _, F10, _, _ = oracle_eval(s, pos)
     assert rel(f10, F10) < TOL["mixed"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_open_fcc_slab_forces(precision):
+    """FCC stand-in (r_cut 5.0, 42 interactions per atom) in a slab open
+    along z: 54 list entries per bulk atom."""
+    s = I.slab_system(I.FCC_CU_LIKE, (8, 8, 5), 4, 5.0, 0.03, 350.0, I.SEED_BASE + 603, n_knots=2000)
+    _, _, F, E, _ = oracle_eval(s)
+    with binding.MD(s, precision=precision) as md:
+        assert md.stats()["max_neighbors"] >= 54
+        assert rel(md.forces(), F) < TOL[precision]
+        pe, _ = md.energy()
+        assert abs(pe - E.sum()) / abs(E.sum()) < TOL[precision]
