@@ -226,13 +226,15 @@ void orc_pot_destroy(orc_pot *p)
 
 static int is_open(int open, int d) { return (open >> d) & 1; }
 
-/* x <- x - L floor(x / L), per coordinate of the periodic axes. */
+/* Periodic image of each coordinate on the periodic axes: a coordinate
+ * already in [0, L) is kept as it is, any other becomes x - L floor(x / L). */
 void orc_wrap(int64_t n, const double box[3], int open, double *pos)
 {
     for (int64_t i = 0; i < n; ++i)
         for (int d = 0; d < 3; ++d) {
             if (is_open(open, d)) continue;
             double x = pos[3 * i + d];
+            if (x >= 0.0 && x < box[d]) continue;
             double q = floor(x / box[d]);
             pos[3 * i + d] = x - box[d] * q;
         }

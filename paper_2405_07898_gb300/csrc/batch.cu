@@ -144,12 +144,7 @@ __device__ void rb_bin(const BatchBufs &B, const RepParam &P, int s)
         for (int a = 0; a < 3; ++a) {
             const double L = P.box[a];
             double x = __dadd_rn(B.xr[s][a][g], B.d[a][g]);
-            if (x >= 0.0 && x < L) {
-            } else if (x < 0.0 && x >= -L) {
-                x = __dadd_rn(x, L);
-            } else if (x >= L && x < 2.0 * L) {
-                x = __dsub_rn(x, L);
-            } else {
+            if (!(x >= 0.0 && x < L)) {  // kept when already in [0, L)
                 const double q = floor(__ddiv_rn(x, L));
                 x = __dsub_rn(x, __dmul_rn(L, q));
             }

@@ -1190,7 +1190,10 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     const double margin = 8.0 * (20.0 * hmax * r_list + 4.0 * r_list * r_list) * eps;
     G.screen_lo = G.rl2 - margin;
     G.screen_hi = G.rl2 + margin;
-    for (int a = 0; a < 3; ++a) G.h_f[a] = (float)G.h[a];
+    for (int a = 0; a < 3; ++a) {
+        G.h_f[a] = (float)G.h[a];
+        G.inv_cell_f[a] = (float)G.inv_cell[a];
+    }
     G.rc2_f = (float)G.rc2;
     G.screen_lo_f = (float)G.screen_lo;
     G.screen_hi_f = (float)G.screen_hi;

@@ -99,6 +99,7 @@ struct Geom {
     int open_mask;       // one bit per open (non-periodic) axis: 1 x, 2 y, 4 z
     // the same in FP32, so that FP32 kernels convert nothing on the FP64 pipe
     float h_f[3];
+    float inv_cell_f[3];  // inv_cell rounded to FP32 (the binning estimate)
     float rc2_f;
     float screen_lo_f, screen_hi_f;
 };

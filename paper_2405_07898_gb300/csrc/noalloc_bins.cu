@@ -43,7 +43,8 @@ __global__ void k_nb_clear(int *count, int ncells)
     if (c < ncells) count[c] = 0;
 }
 
-// wrap x - L floor(x/L), then c_d = min(floor(x_d n_d / L_d), n_d - 1)
+// periodic image (x kept in [0, L), else x - L floor(x/L)), then
+// c_d = min(floor(x_d n_d / L_d), n_d - 1)
 __global__ void k_nb_bin(const double *pos, int n, BinGeom G, int *cell_of, int *rank, int *count)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -53,8 +54,10 @@ __global__ void k_nb_bin(const double *pos, int n, BinGeom G, int *cell_of, int 
     for (int a = 0; a < 3; ++a) {
         double L = G.box[a];
         double x = pos[3 * (size_t)i + a];
-        double q = floor(__ddiv_rn(x, L));
-        x = __dsub_rn(x, __dmul_rn(L, q));
+        if (!(x >= 0.0 && x < L)) {
+            double q = floor(__ddiv_rn(x, L));
+            x = __dsub_rn(x, __dmul_rn(L, q));
+        }
         double y = floor(__dmul_rn(x, G.inv_cell[a]));
         c[a] = isfinite(y) ? (int)fmax(fmin(y, (double)(G.ncell[a] - 1)), 0.0) : 0;
     }

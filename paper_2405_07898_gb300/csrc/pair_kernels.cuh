@@ -641,27 +641,33 @@ __device__ __forceinline__ void copy_rows(const float4 *coef2, int nint, float4 
 template <bool ENERGY, int TPA>
 __global__ void __launch_bounds__(256) k_density_tab(Bufs<float> B, Geom G, Launch L)
 {
+    const DevState *st = B.st;
+    const int sp = st->sp, s = st->set;
+    const int width = blockDim.x / TPA, l = threadIdx.x % TPA;
+    const int ntiles = (L.n + width - 1) / width;
+    // the warp's list columns are asked of L2 one tile ahead; the first
+    // tile's request overlaps the table copy
+    const int wa = (threadIdx.x >> 5) * (32 / TPA), ncol = min(st->max_nnb, L.cap);
+    prefetch_warp_streams<float, false>(B, L, s, blockIdx.x * width + wa, 32 / TPA, ncol);
     float4 *f_rows = reinterpret_cast<float4 *>(dyn);
     const int nint = B.tables->fphi.nint;
     copy_rows(B.coef2, nint, f_rows, nullptr);
     __syncthreads();
     float h[3];
     load_h<float>(G, h);
-    const DevState *st = B.st;
-    const int sp = st->sp, s = st->set;
     float4 *sw = B.shadow[sp];
     const float rc2 = g_rc2<float>(G);
-    const int width = blockDim.x / TPA, l = threadIdx.x % TPA;
-    const int ntiles = (L.n + width - 1) / width;
     const TabShared tab{f_rows, nullptr};
     float e_embed = 0.f;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (tile + (int)gridDim.x < ntiles)
+            prefetch_warp_streams<float, false>(B, L, s, (tile + gridDim.x) * width + wa, 32 / TPA, ncol);
         const int i = tile * width + threadIdx.x / TPA;
         const bool active = i < L.n;
         float rho = 0.f;
         if (active)
-            rho = density_lane<float, false, TPA, 2>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], ListGlobal{B.list + i, L.ld},
-                                                     GlobalFetch<float>{sw}, tab);
+            rho = density_lane<float, false, TPA, PairsInFlight<false>::density>(
+                B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], ListGlobal{B.list + i, L.ld}, GlobalFetch<float>{sw}, tab);
         rho = lane_sum<TPA>(rho);
         if (active && l == 0) e_embed += embed<float>(B, sw, i, 0, rho);
     }
@@ -674,6 +680,12 @@ __global__ void __launch_bounds__(256) k_density_tab(Bufs<float> B, Geom G, Laun
 template <int MODE, bool ENERGY, int TPA>
 __global__ void __launch_bounds__(256) k_force_tab(Bufs<float> B, Geom G, Launch L)
 {
+    const DevState *st = B.st;
+    const int sp = st->sp, s = st->set;
+    const int width = blockDim.x / TPA, l = threadIdx.x % TPA;
+    const int ntiles = (L.n + width - 1) / width;
+    const int wa = (threadIdx.x >> 5) * (32 / TPA), ncol = min(st->max_nnb, L.cap);
+    prefetch_warp_streams<float, true>(B, L, s, blockIdx.x * width + wa, 32 / TPA, ncol);
     const int nint = B.tables->fphi.nint;
     float4 *f_rows = reinterpret_cast<float4 *>(dyn);
     float4 *phi_rows = f_rows + nint;
@@ -681,22 +693,20 @@ __global__ void __launch_bounds__(256) k_force_tab(Bufs<float> B, Geom G, Launch
     __syncthreads();
     float h[3];
     load_h<float>(G, h);
-    const DevState *st = B.st;
-    const int sp = st->sp, s = st->set;
     const float4 *sw = B.shadow[sp];
     const float rc2 = g_rc2<float>(G);
-    const int width = blockDim.x / TPA, l = threadIdx.x % TPA;
-    const int ntiles = (L.n + width - 1) / width;
     const TabShared tab{f_rows, phi_rows};
     float e7[7] = {0, 0, 0, 0, 0, 0, 0};
     double ke = 0.0;
     float d2max = 0.f;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (tile + (int)gridDim.x < ntiles)
+            prefetch_warp_streams<float, true>(B, L, s, (tile + gridDim.x) * width + wa, 32 / TPA, ncol);
         const int i = tile * width + threadIdx.x / TPA;
         const bool active = i < L.n;
         float f[3] = {0, 0, 0};
         if (active)
-            force_lane<float, false, ENERGY, TPA, 2>(B, L, h, rc2, s, B.nnb + i, l, 0, sw[i],
+            force_lane<float, false, ENERGY, TPA, PairsInFlight<false>::force>(B, L, h, rc2, s, B.nnb + i, l, 0, sw[i],
                                                      ListGlobal{B.list + i, L.ld}, GlobalFetch<float>{sw}, f, e7, tab);
 #pragma unroll
         for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);

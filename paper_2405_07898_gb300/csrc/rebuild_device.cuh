@@ -10,10 +10,38 @@
 namespace eammd {
 namespace {
 
-// Wrap x = xr + d into [0, L) exactly as x - L floor(x / L) (for |x| < 2L the
-// branch form below gives the same bits) on periodic axes, then bin:
-// c_d = floor(x_d n_d/L_d) clamped to [0, n_d - 1].
-// The slot inside the cell is the arrival order (fixed by sort_cell).
+// x as a float truncated toward zero, from its bits by integer operations
+// (the FP64 pipe of this GPU is narrow): 0 below 2^-126, +-inf above the
+// float range.
+__device__ __forceinline__ float trunc_to_float(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    if (e < 897u) return 0.f;
+    if (e > 1150u) return __uint_as_float((hi & 0x80000000u) | 0x7f800000u);
+    return __uint_as_float((hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
+// Cell index floor(RN(x inv)) clamped to [0, n - 1], for finite x.  The FP32
+// product of the truncated x and the rounded inv is within 2^-21.8 |q| of the
+// FP64 product (truncation 2^-23, two roundings 2^-24 each); where it lies
+// farther than 2^-20 max(|q|, 1) from every integer both have the same floor,
+// elsewhere the FP64 product decides.
+__device__ __forceinline__ int cell_index(double x, double inv, float inv_f, int n)
+{
+    const float q32 = trunc_to_float(x) * inv_f;
+    const float f = floorf(q32), frac = q32 - f;
+    const float tol = 0x1p-20f * fmaxf(fabsf(q32), 1.0f);
+    if (frac > tol && frac < 1.0f - tol) return min(max((int)f, 0), n - 1);
+    const double q = floor(__dmul_rn(x, inv));
+    return (int)fmax(fmin(q, (double)(n - 1)), 0.0);
+}
+
+// Periodic image of x = xr + d on periodic axes: kept when already in
+// [0, L), else x - L floor(x / L); then bin: c_d = floor(x_d n_d/L_d) clamped
+// to [0, n_d - 1].  The box test compares bit patterns (non-negative doubles
+// order as their bits; -0 is inside).  The slot inside the cell is the
+// arrival order (fixed by sort_cell).
 template <class R>
 __device__ __forceinline__ void bin_atom(const Bufs<R> &B, const Geom &G, int s, int i)
 {
@@ -23,21 +51,16 @@ __device__ __forceinline__ void bin_atom(const Bufs<R> &B, const Geom &G, int s,
     for (int a = 0; a < 3; ++a) {
         double L = G.box[a];
         double x = __dadd_rn(B.xr[s][a][i], B.d[a][i]);
-        if (((G.open_mask >> a) & 1) || (x >= 0.0 && x < L)) {
-            // open axis: not wrapped (outside the box, the edge cell takes it)
-        } else if (x < 0.0 && x >= -L) {
-            x = __dadd_rn(x, L);
-        } else if (x >= L && x < 2.0 * L) {
-            x = __dsub_rn(x, L);
-        } else {
-            double q = floor(__ddiv_rn(x, L));
+        const long long xb = __double_as_longlong(x);
+        const bool inside = (xb >= 0 && xb < __double_as_longlong(L)) || xb == (long long)0x8000000000000000ull;
+        if (!((G.open_mask >> a) & 1) && !inside) {
+            // (open axis: not wrapped; outside the box, the edge cell takes it)
+            const double q = floor(__ddiv_rn(x, L));
             x = __dsub_rn(x, __dmul_rn(L, q));
         }
-        finite = finite && isfinite(x);
+        finite = finite && ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff;
         B.xw[a][i] = x;
-        double q = floor(__dmul_rn(x, G.inv_cell[a]));
-        int ca = finite ? (int)fmax(fmin(q, (double)(G.ncell[a] - 1)), 0.0) : 0;
-        c[a] = ca;
+        c[a] = finite ? cell_index(x, G.inv_cell[a], G.inv_cell_f[a], G.ncell[a]) : 0;
     }
     if (!finite) atomicOr(&B.st->error, ERR_NONFINITE);
     int cell = (c[2] * G.ncell[1] + c[1]) * G.ncell[0] + c[0];

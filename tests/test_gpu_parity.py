@@ -47,6 +47,41 @@ def test_cells_and_neighbor_list_bit_exact(c1, precision):
         np.testing.assert_array_equal(js, ojs)  # same stencil order, same order in a cell
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cells_on_cell_boundaries_bit_exact(c1, precision):
+    """Coordinates on cell boundaries k L/n, one ulp either side of them, at
+    -0, just below 0 and just below L: the binning's FP32 estimate must hand
+    every case it cannot settle to the FP64 product, so the bins stay those of
+    the definition."""
+    r_list = c1.pot.r_list
+    nc = O.cell_dims(c1.box, r_list)
+    pos = O.wrap(c1.pos, c1.box).copy()
+    moved = 0
+    for a in range(3):
+        h = c1.box[a] / nc[a]
+        k = np.rint(pos[:, a] / h)
+        near = np.abs(pos[:, a] - k * h) < 0.05
+        for m, i in enumerate(np.flatnonzero(near)):
+            b = k[i] * h
+            pos[i, a] = (b, np.nextafter(b, -np.inf), np.nextafter(b, np.inf))[m % 3]
+            moved += 1
+    i0 = np.argsort(pos[:, 0])[:4]
+    pos[i0, 0] = (0.0, -0.0, -1e-300, -5e-324)
+    i1 = np.argsort(pos[:, 1])[-2:]
+    pos[i1, 1] = (np.nextafter(c1.box[1], 0), c1.box[1])
+    assert moved > 100
+    s = I.System(box=c1.box, pos=pos, vel=c1.vel, types=c1.types, pot=c1.pot)
+    w = O.wrap(s.pos, s.box)
+    with binding.MD(s, precision=precision) as md:
+        got = md.cells()
+        off, js = md.neighbors()
+    for g, o in zip(got, O.cells(w, s.box, r_list)):
+        np.testing.assert_array_equal(g, o)
+    ooff, ojs = O.neighbors_cells(w, s.box, r_list)
+    np.testing.assert_array_equal(off, ooff)
+    np.testing.assert_array_equal(js, ojs)
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("mixed", MIXED_TOL)])
 def test_initial_forces_energy_virial(c1, precision, tol):
     rho, Fp, F, E, W = oracle_eval(c1)

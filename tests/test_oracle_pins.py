@@ -113,6 +113,13 @@ def test_wrap_and_cells_stable_counting_sort():
     w = O.wrap(pos, box)
     assert (w >= 0).all() and (w < box).all()
     np.testing.assert_allclose(np.mod(pos, box), w, atol=1e-12)
+    inside = (pos >= 0) & (pos < box)
+    assert inside.any() and (~inside).any()
+    np.testing.assert_array_equal(w[inside], pos[inside])  # in-box coordinates are kept bit for bit
+    # one ulp below the box edge stays (x / L may round up to 1: the image
+    # formula alone would give a negative coordinate there)
+    edge = np.tile(np.nextafter(box, 0), (1, 1))
+    np.testing.assert_array_equal(O.wrap(edge, box), edge)
     nc, start, atoms = O.cells(w, box, 4.8)
     assert tuple(nc) == (3, 3, 4)
     c = np.minimum(np.floor(w * (nc / box)).astype(int), nc - 1)
