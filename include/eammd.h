@@ -167,7 +167,11 @@ enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2, MD_SCH
  *   stage_capacity   records a row-staged block holds; 0 = 1.1 x the most
  *                    that any 3 x 3 block of rows holds at md_create, + 32.
  *                    Must fit the shared memory of a block (160 KB of
- *                    16-byte (mixed) or 32-byte (fp64) records). */
+ *                    16-byte (mixed) or 32-byte (fp64) records).
+ *   batch_schedule   batches only: 0 = threads per block and resident
+ *                    blocks per SM timed at md_batch_create (unless
+ *                    lanes_per_atom > 0, which takes 512 x 1); 1..5 =
+ *                    512 x 1, 256 x 2, 256 x 3, 1024 x 1, 512 x 2. */
 typedef struct {
     int32_t precision;
     int32_t rebuild_every;
@@ -184,6 +188,7 @@ typedef struct {
     int32_t persistent;
     int32_t wait_limit_us;
     int32_t open_axes;
+    int32_t batch_schedule;
 } md_options;
 
 void md_options_default(md_options *opt);

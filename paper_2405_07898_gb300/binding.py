@@ -59,7 +59,8 @@ class Options(C.Structure):
                 ("stage_capacity", C.c_int32),
                 ("persistent", C.c_int32),
                 ("wait_limit_us", C.c_int32),
-                ("open_axes", C.c_int32)]
+                ("open_axes", C.c_int32),
+                ("batch_schedule", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -403,7 +404,7 @@ class MDBatch:
     one-type potentials; identical potentials are shared."""
 
     def __init__(self, systems, rebuild_every: int = 10, list_capacity: int = 0, use_graphs: bool = True,
-                 use_torch: bool | None = None):
+                 use_torch: bool | None = None, schedule: int = 0):
         L = load()
         self._L = L
         self._keep = []
@@ -439,6 +440,7 @@ class MDBatch:
         opt.rebuild_every = rebuild_every
         opt.list_capacity = list_capacity
         opt.use_graphs = 1 if use_graphs else 0
+        opt.batch_schedule = schedule
         if use_torch is None:
             try:
                 import torch

@@ -27,7 +27,7 @@
 namespace eammd {
 namespace {
 
-constexpr int kMaxBatchWarps = 16;  // blocks of up to 512 threads
+constexpr int kMaxBatchWarps = 32;  // blocks of up to 1024 threads
 
 struct RepParam {
     int n;          // atoms
@@ -86,6 +86,7 @@ struct Smem {
     double red_d[kMaxBatchWarps];
     float red_f[kMaxBatchWarps];
     int red_i[32];
+    int chunk;
     int carry;
     int need;
     int rep;
@@ -185,7 +186,7 @@ __device__ void rb_scan(const BatchBufs &B, const RepParam &P, Smem &S)
                 if (lane >= o) wi += y;
             }
             S.red_i[lane] = wi - w;  // exclusive prefix of the warp totals
-            if (lane == 31) S.red_i[31] = wi;  // chunk total (at most 16 warps)
+            if (lane == 31) S.chunk = wi;
         }
         __syncthreads();
         const int excl = S.carry + S.red_i[warp] + incl - v;
@@ -193,7 +194,7 @@ __device__ void rb_scan(const BatchBufs &B, const RepParam &P, Smem &S)
             start[c] = excl;
             cnt[c] = 0;
         }
-        const int chunk_total = S.red_i[31];
+        const int chunk_total = S.chunk;
         __syncthreads();
         if (threadIdx.x == 0) S.carry += chunk_total;
         __syncthreads();
@@ -696,13 +697,16 @@ bool balloc_n(md_batch *b, T *&p, size_t count)
 struct BatchSchedule {
     int block, min_blocks;
 };
-constexpr BatchSchedule kSchedules[3] = {{512, 1}, {256, 2}, {256, 3}};
+constexpr BatchSchedule kSchedules[5] = {{512, 1}, {256, 2}, {256, 3}, {1024, 1}, {512, 2}};
+constexpr int kNumSchedules = 5;
 
 md_status batch_launch(md_batch *b, int mode, int nsteps, double dt)
 {
     BCK(cudaMemsetAsync(b->B.queue, 0, sizeof(int), b->stream));
     switch (b->schedule) {
     case 1: k_batch<256, 2><<<b->grid, 256, 0, b->stream>>>(b->B, mode, nsteps, dt); break;
+    case 3: k_batch<1024, 1><<<b->grid, 1024, 0, b->stream>>>(b->B, mode, nsteps, dt); break;
+    case 4: k_batch<512, 2><<<b->grid, 512, 0, b->stream>>>(b->B, mode, nsteps, dt); break;
     case 2: k_batch<256, 3><<<b->grid, 256, 0, b->stream>>>(b->B, mode, nsteps, dt); break;
     default: k_batch<512, 1><<<b->grid, 512, 0, b->stream>>>(b->B, mode, nsteps, dt); break;
     }
@@ -748,6 +752,8 @@ md_status md_batch_create(int32_t nrep, const md_replica *reps, int32_t npot, co
     if (o.open_axes != 0) return bad(MD_ERR_ARG, "batch replicas are periodic (open_axes must be 0)");
     if ((o.alloc == nullptr) != (o.free == nullptr)) return bad(MD_ERR_ARG, "alloc and free go together");
     if (o.rebuild_every < 1) o.rebuild_every = 10;
+    if (o.batch_schedule < 0 || o.batch_schedule > kNumSchedules)
+        return bad(MD_ERR_ARG, "batch_schedule must be 0 (tuned) or 1..5");
     // potentials: one type each, f and phi on one grid (fused rows)
     std::vector<double> rowsF, rows2;
     std::vector<SplineDesc<float>> dF(npot), dfphi(npot);
@@ -936,6 +942,8 @@ md_status md_batch_create(int32_t nrep, const md_replica *reps, int32_t npot, co
         int per_sm = 1;
         if (sched == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<256, 2>, 256, 0);
         else if (sched == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<256, 3>, 256, 0);
+        else if (sched == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<1024, 1>, 1024, 0);
+        else if (sched == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<512, 2>, 512, 0);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<512, 1>, 512, 0);
         return std::max(1, std::min(nrep, std::max(per_sm, 1) * sms));
     };
@@ -946,7 +954,10 @@ md_status md_batch_create(int32_t nrep, const md_replica *reps, int32_t npot, co
     // schedule autotuner: right after the initial build every replica is
     // rebuild_every steps from its next build, so rebuild_every - 1 steps of
     // dt = 0 change nothing but the counters, which are restored afterwards
-    if (rc == MD_OK && o.rebuild_every > 1 && o.lanes_per_atom == 0) {
+    if (rc == MD_OK && o.batch_schedule > 0) {
+        b->schedule = o.batch_schedule - 1;
+        b->grid = grid_for(b->schedule);
+    } else if (rc == MD_OK && o.rebuild_every > 1 && o.lanes_per_atom == 0) {
         const int trial = std::min(o.rebuild_every - 1, 8);
         float best = 1e30f;
         int best_s = 0;
@@ -954,7 +965,7 @@ md_status md_batch_create(int32_t nrep, const md_replica *reps, int32_t npot, co
         cudaEventCreate(&t0);
         cudaEventCreate(&t1);
         for (int round = 0; round < 2 && rc == MD_OK; ++round)
-            for (int sc = 0; sc < 3 && rc == MD_OK; ++sc) {
+            for (int sc = 0; sc < kNumSchedules && rc == MD_OK; ++sc) {
                 b->schedule = sc;
                 b->grid = grid_for(sc);
                 cudaEventRecord(t0, b->stream);

@@ -90,3 +90,26 @@ def test_rejects_bad_replicas():
     with pytest.raises(binding.MDError) as e:
         binding.MDBatch([s, tiny])
     assert e.value.status == -2
+    with pytest.raises(binding.MDError) as e:
+        binding.MDBatch([s], schedule=6)
+    assert e.value.status == -1
+
+
+def test_every_block_shape_gives_the_same_trajectories():
+    """Each threads-per-block x blocks-per-SM shape of the batch launch, on a
+    replica whose cell scan spans several 1,024-cell chunks (so every warp of
+    a 1,024-thread block holds cells): forces meet the oracle bar, and
+    positions after 20 steps are bitwise those of every other shape."""
+    systems = [I.thermal_system(I.BCC_TA_LIKE, (28, 28, 28), 0.02, 600.0, 111),
+               I.thermal_system(I.FCC_CU_LIKE, (6, 6, 6), 0.02, 500.0, 112)]
+    refs = [oracle_state(s)[2] for s in systems]
+    out = []
+    for sched in range(1, 6):
+        with binding.MDBatch(systems, schedule=sched) as b:
+            for r in range(len(systems)):
+                assert rel(b.get_state(r)[2], refs[r]) < MIXED_TOL, (sched, r)
+            b.step(20, 2.0)
+            out.append([b.get_state(r)[0] for r in range(len(systems))])
+    for o in out[1:]:
+        for a, c in zip(o, out[0]):
+            np.testing.assert_array_equal(a, c)
