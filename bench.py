@@ -320,9 +320,14 @@ def run_batch(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    if args.profiler_range:
+        torch.cuda.profiler.start()
     e0.record(b.stream)
     b.step(args.batch_steps, DT_FS)
     e1.record(b.stream)
+    if args.profiler_range:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     b.energy()
     ms = e0.elapsed_time(e1)
     info = b.info()
