@@ -214,7 +214,7 @@ def run_ours(args):
     if rank == 0:
         cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu_baseline) else None
         line = {
-            "metric": "timesteps/s at 800k atoms (mixed precision EAM MD)",
+            "metric": f"timesteps/s at 800k atoms ({'mixed precision' if args.precision == 'mixed' else 'FP64'} EAM MD)",
             "value": ts_per_s,
             "unit": "timesteps/s",
             "n_gpus": world,
@@ -224,9 +224,10 @@ def run_ours(args):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32+f64",
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64",
             "data": "synthetic: seeded BCC lattice, Gaussian displacements, Maxwell velocities",
-            "config": {"workload": WORKLOAD if not args.cells else system.label + "_mixed", "atoms": n, "md_steps_per_step": MD_STEPS_PER_BENCH_STEP,
+            "config": {"workload": (WORKLOAD if not args.cells else system.label + "_mixed").replace(
+                           "_mixed", "_" + args.precision), "atoms": n, "md_steps_per_step": MD_STEPS_PER_BENCH_STEP,
                        "dt_fs": DT_FS, "rebuild_every": 10, "precision": args.precision,
                        "list": "full Verlet list, r_list 4.8 A, 26 entries/atom",
                        "l2": "working set ~0.35 GB > L2 (no flush needed)",
