@@ -70,6 +70,7 @@ struct BatchBufs {
     int *nnb;
     const float4 *coef;                  // F rows of every potential
     const float4 *coef2;                 // fused f | phi rows of every potential
+    const float4 *coef_f;                // the f rows alone (density pass), same interval index
     const SplineDesc<float> *fphi, *Fd;  // per potential (offsets in rows)
     const RepParam *par;
     RepState *st;
@@ -449,7 +450,7 @@ __device__ void run_replica(const BatchBufs &B, Smem &S, int r, int mode, int ns
                         inv_r(r2, rinv, rr);
                         float t;
                         const int kk = segment(g, rr, t);
-                        const float4 c = cf2[2 * (g.offset + kk)];
+                        const float4 c = B.coef_f[g.offset + kk];
                         rho += fmaf(t, fmaf(t, fmaf(t, c.w, c.z), c.y), c.x);
                     }
                 }
@@ -755,7 +756,7 @@ md_status md_batch_create(int32_t nrep, const md_replica *reps, int32_t npot, co
     if (o.batch_schedule < 0 || o.batch_schedule > kNumSchedules)
         return bad(MD_ERR_ARG, "batch_schedule must be 0 (tuned) or 1..5");
     // potentials: one type each, f and phi on one grid (fused rows)
-    std::vector<double> rowsF, rows2;
+    std::vector<double> rowsF, rows2, rowsf;
     std::vector<SplineDesc<float>> dF(npot), dfphi(npot);
     for (int q = 0; q < npot; ++q) {
         const md_potential &pt = pots[q];
@@ -779,6 +780,7 @@ md_status md_batch_create(int32_t nrep, const md_replica *reps, int32_t npot, co
         for (int k = 0; k < f.n - 1; ++k) {
             for (int c = 0; c < 4; ++c) rows2.push_back(rf[4 * (size_t)k + c]);
             for (int c = 0; c < 4; ++c) rows2.push_back(rp[4 * (size_t)k + c]);
+            for (int c = 0; c < 4; ++c) rowsf.push_back(rf[4 * (size_t)k + c]);
         }
         dfphi[q] = batch_desc(f, off2, &rf[rf.size() - 4], &rf[0]);
     }
@@ -877,11 +879,12 @@ md_status md_batch_create(int32_t nrep, const md_replica *reps, int32_t npot, co
          balloc_n(b, B.cell_atoms, N) && balloc_n(b, B.nnb, N);
     ok = ok && balloc_n(b, B.count, (size_t)cell_off) && balloc_n(b, B.cell_start, (size_t)cs_off);
     ok = ok && balloc_n(b, B.list, (size_t)list_off);
-    float4 *coef = nullptr, *coef2 = nullptr;
+    float4 *coef = nullptr, *coef2 = nullptr, *coef_f = nullptr;
     SplineDesc<float> *dfp = nullptr, *dFd = nullptr;
     RepParam *par = nullptr;
     int *order = nullptr;
     ok = ok && balloc_n(b, coef, rowsF.size() / 4) && balloc_n(b, coef2, rows2.size() / 4) &&
+         balloc_n(b, coef_f, rowsf.size() / 4) &&
          balloc_n(b, dfp, (size_t)npot) && balloc_n(b, dFd, (size_t)npot) && balloc_n(b, par, (size_t)nrep) &&
          balloc_n(b, B.st, (size_t)nrep) && balloc_n(b, order, (size_t)nrep) && balloc_n(b, B.queue, 1) &&
          balloc_n(b, b->stage, 9 * (size_t)b->max_n);
@@ -897,6 +900,7 @@ md_status md_batch_create(int32_t nrep, const md_replica *reps, int32_t npot, co
     };
     cudaError_t ce = up4(coef, rowsF);
     if (ce == cudaSuccess) ce = up4(coef2, rows2);
+    if (ce == cudaSuccess) ce = up4(coef_f, rowsf);
     if (ce == cudaSuccess) ce = cudaMemcpy(dfp, dfphi.data(), sizeof(SplineDesc<float>) * npot, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemcpy(dFd, dF.data(), sizeof(SplineDesc<float>) * npot, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemcpy(par, b->par.data(), sizeof(RepParam) * nrep, cudaMemcpyHostToDevice);
@@ -928,6 +932,7 @@ md_status md_batch_create(int32_t nrep, const md_replica *reps, int32_t npot, co
     }
     B.coef = coef;
     B.coef2 = coef2;
+    B.coef_f = coef_f;
     B.fphi = dfp;
     B.Fd = dFd;
     B.par = par;

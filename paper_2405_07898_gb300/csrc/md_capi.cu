@@ -202,6 +202,7 @@ bool alloc_buffers(md_ctx *ctx, const std::vector<double> &rows, const std::vect
     if (!ok) return false;
     B.coef = coef;
     B.coef2 = coef2;
+    B.coef_f = tables.fused ? coef2 + 2 * (size_t)tables.fphi.nint : coef2;
     B.tables = tab;
     B.st = ctx->st;
     auto upload = [](R4 *dst_dev, const std::vector<double> &src) -> bool {
@@ -580,6 +581,10 @@ md_status build_tables(md_ctx *ctx, const md_potential *pot, std::vector<double>
             for (int c = 0; c < 4; ++c) rows2.push_back(rows[4 * ((size_t)tab.f[0].offset + k) + c]);
             for (int c = 0; c < 4; ++c) rows2.push_back(rows[4 * ((size_t)tab.phi[0].offset + k) + c]);
         }
+        // then the f rows alone, for the density pass: twice as many
+        // intervals per cache line as in the interleaved rows
+        for (int k = 0; k < f0.n - 1; ++k)
+            for (int c = 0; c < 4; ++c) rows2.push_back(rows[4 * ((size_t)tab.f[0].offset + k) + c]);
     }
     return MD_OK;
 }

@@ -134,6 +134,7 @@ struct Bufs {
     DevState *st;
     const R4 *coef;
     const R4 *coef2;     // fused f | phi rows (single-type fast path)
+    const R4 *coef_f;    // the f rows alone (coef2 + 2 nint), read by the density pass
     const Tables<R> *tables;
 };
 

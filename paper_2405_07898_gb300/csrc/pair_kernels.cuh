@@ -85,13 +85,16 @@ struct StagedFetch {
 };
 
 // Where the spline rows of the one-type path are read from: coef2 in device
-// memory (row 2k: f, row 2k+1: phi, both in one 32-byte load) or a copy in
-// shared memory with the f and phi rows in two arrays, so that 16-byte reads
-// at scattered rows spread over all banks.
+// memory (row 2k: f, row 2k+1: phi, both in one 32-byte load; the density
+// pass reads the f rows alone from coef_f, where a 128-byte line holds eight
+// intervals instead of four) or a copy in shared memory with the f and phi
+// rows in two arrays, so that 16-byte reads at scattered rows spread over
+// all banks.
 template <class R>
 struct TabGlobal {
     const typename V4<R>::T *coef2;
-    __device__ __forceinline__ typename V4<R>::T f(int kk) const { return coef2[2 * kk]; }
+    const typename V4<R>::T *coef_f;  // f rows alone: more intervals per cache line
+    __device__ __forceinline__ typename V4<R>::T f(int kk) const { return coef_f[kk]; }
     __device__ __forceinline__ void fphi(int kk, typename V4<R>::T &cf, typename V4<R>::T &cp) const
     {
         load_row2<R>(coef2 + 2 * kk, cf, cp);
@@ -451,10 +454,10 @@ __global__ void __launch_bounds__(256) k_density(Bufs<R> B, Geom G, Launch L)
     if (active) {
         if (tiled)
             rho = density_lane<R, MULTI, TPA, U>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], ListTile{tile + (i - i0), width},
-                                                 GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2});
+                                                 GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2, B.coef_f});
         else
             rho = density_lane<R, MULTI, TPA, U>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], ListGlobal{B.list + i, L.ld},
-                                                 GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2});
+                                                 GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2, B.coef_f});
     }
     rho = lane_sum<TPA>(rho);
     R e_embed = (R)0;
@@ -489,10 +492,10 @@ __global__ void __launch_bounds__(256) k_force(Bufs<R> B, Geom G, Launch L)
     if (active) {
         if (tiled)
             force_lane<R, MULTI, ENERGY, TPA, U>(B, L, h, rc2, s, B.nnb + i, l, ti, sw[i], ListTile{tile + (i - i0), width},
-                                                 GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2});
+                                                 GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2, B.coef_f});
         else
             force_lane<R, MULTI, ENERGY, TPA, U>(B, L, h, rc2, s, B.nnb + i, l, ti, sw[i], ListGlobal{B.list + i, L.ld},
-                                                 GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2});
+                                                 GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2, B.coef_f});
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);
@@ -568,10 +571,10 @@ __global__ void __launch_bounds__(256) k_density_rows(Bufs<R> B, Geom G, Launch 
                 const ListGlobal list{B.list + i, L.ld};
             if (staged)
                 rho = density_lane<R, false, TPA, 4>(B, h, rc2, s, B.nnb + i, L.cap, l, stage[i - base[4]], list,
-                                                     StagedFetch<R>{stage, base}, TabGlobal<R>{B.coef2});
+                                                     StagedFetch<R>{stage, base}, TabGlobal<R>{B.coef2, B.coef_f});
             else
                 rho = density_lane<R, false, TPA, 4>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], list, GlobalFetch<R>{sw},
-                                                     TabGlobal<R>{B.coef2});
+                                                     TabGlobal<R>{B.coef2, B.coef_f});
         }
         rho = lane_sum<TPA>(rho);
         if (active && l == 0) e_embed += embed<R>(B, sw, i, 0, rho);
@@ -609,10 +612,10 @@ __global__ void __launch_bounds__(256) k_force_rows(Bufs<R> B, Geom G, Launch L)
                 const ListGlobal list{B.list + i, L.ld};
             if (staged)
                 force_lane<R, false, ENERGY, TPA, 4>(B, L, h, rc2, s, B.nnb + i, l, 0, stage[i - base[4]], list,
-                                                     StagedFetch<R>{stage, base}, f, e7, TabGlobal<R>{B.coef2});
+                                                     StagedFetch<R>{stage, base}, f, e7, TabGlobal<R>{B.coef2, B.coef_f});
             else
                 force_lane<R, false, ENERGY, TPA, 4>(B, L, h, rc2, s, B.nnb + i, l, 0, sw[i], list, GlobalFetch<R>{sw}, f,
-                                                     e7, TabGlobal<R>{B.coef2});
+                                                     e7, TabGlobal<R>{B.coef2, B.coef_f});
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);

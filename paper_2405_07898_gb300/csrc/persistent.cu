@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256) k_steps(Bufs<R> B, Geom G, Launch L, long
                 R rho = (R)0;
                 if (active)
                     rho = density_lane<R, MULTI, TPA, UD>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], ListGlobal{B.list + i, L.ld},
-                                                          GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2});
+                                                          GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2, B.coef_f});
                 rho = lane_sum<TPA>(rho);
                 if (active && l == 0) e_embed += embed<R>(B, sw, i, ti, rho);
             }
@@ -192,14 +192,14 @@ __global__ void __launch_bounds__(256) k_steps(Bufs<R> B, Geom G, Launch L, long
                 if (last) {
                     if (active)
                         force_lane<R, MULTI, true, TPA, UF>(B, L, h, rc2, s, B.nnb + i, l, ti, sw[i], list,
-                                                            GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2});
+                                                            GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2, B.coef_f});
 #pragma unroll
                     for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);
                     if (active) integrate<R, MODE_CLOSE, true, TPA>(B, L, s, sp, i, l, ti, f, ke, d2);
                 } else {
                     if (active)
                         force_lane<R, MULTI, false, TPA, UF>(B, L, h, rc2, s, B.nnb + i, l, ti, sw[i], list,
-                                                             GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2});
+                                                             GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2, B.coef_f});
 #pragma unroll
                     for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);
                     if (active) integrate<R, MODE_CLOSE_OPEN, false, TPA>(B, L, s, sp, i, l, ti, f, ke, d2);
