@@ -257,10 +257,9 @@ md_status read_state(md_ctx *ctx)
     return MD_OK;
 }
 
-md_status check_device_errors(md_ctx *ctx)
+// The error flags of the device state last read into st_host.
+md_status state_errors(md_ctx *ctx)
 {
-    md_status rc = read_state(ctx);
-    if (rc != MD_OK) return rc;
     unsigned int e = ctx->st_host->error;
     if (e & ERR_LIST_OVERFLOW)
         return ctx->fail(MD_ERR_LIST_OVERFLOW, "an atom had more neighbours (" +
@@ -269,6 +268,13 @@ md_status check_device_errors(md_ctx *ctx)
     if (e & ERR_NONFINITE) return ctx->fail(MD_ERR_NONFINITE, "non-finite position or force");
     if (e & ERR_TIMEOUT) return ctx->fail(MD_ERR_TIMEOUT, "a bounded device wait gave up");
     return MD_OK;
+}
+
+md_status check_device_errors(md_ctx *ctx)
+{
+    md_status rc = read_state(ctx);
+    if (rc != MD_OK) return rc;
+    return state_errors(ctx);
 }
 
 // Rebuild + density + force (no integration) + reduction at the current
@@ -330,7 +336,8 @@ md_status load_and_measure(md_ctx *ctx, const double *pos, const double *vel, in
         }
         break;
     }
-    md_status rc = check_device_errors(ctx);
+    // the state read last in the loop is the current one
+    md_status rc = state_errors(ctx);
     if (rc != MD_OK) return rc;
     // rebuilds are counted from here on
     DevState hs = *ctx->st_host;
