@@ -21,13 +21,19 @@ from . import inputs as I
 
 
 class ForceMatch:
-    """Loss and knot gradient over a set of single-type configurations."""
+    """Loss and knot gradient over a set of single-type configurations.
 
-    def __init__(self, problem: I.FitProblem, reference: I.Potential | None = None):
+    workers: contexts per configuration size, each on its own stream and
+    host thread, so that the small kernels of several configurations share
+    the GPU; per-configuration results are summed in configuration order, so
+    the loss and gradient do not depend on the number of workers."""
+
+    def __init__(self, problem: I.FitProblem, reference: I.Potential | None = None, workers: int = 4):
         self.problem = problem
         self.w = problem.w
         n = problem.n_knots
         self.sizes = (n, n, n)
+        self.workers = max(1, int(workers))
         ref_pot = reference if reference is not None else I.johnson_potential(problem.params)
         self._ref_ctx = {}
         self._ctx = {}
@@ -38,7 +44,8 @@ class ForceMatch:
             m = pos.shape[0]
             if m not in self._ref_ctx:
                 self._ref_ctx[m] = binding.MD(self._system(pos, box, ref_pot), precision="fp64")
-                self._ctx[m] = binding.MD(self._system(pos, box, pot0), precision="fp64")
+                self._ctx[m] = [binding.MD(self._system(pos, box, pot0), precision="fp64")
+                                for _ in range(self.workers)]
             ref = self._ref_ctx[m]
             ref.set_state(pos, None, 0)
             e_ref = ref.energy()[0]  # potential energy
@@ -46,6 +53,10 @@ class ForceMatch:
         for c in self._ref_ctx.values():
             c.close()
         self._ref_ctx = {}
+        self._pool = None
+        if self.workers > 1:
+            from concurrent.futures import ThreadPoolExecutor
+            self._pool = ThreadPoolExecutor(max_workers=self.workers)
         self._theta = theta0.copy()
 
     @staticmethod
@@ -59,27 +70,49 @@ class ForceMatch:
         if np.array_equal(theta, self._theta):
             return
         pot = self.problem.potential(theta)
-        for c in self._ctx.values():
-            c.set_potential(pot)
+        for cs in self._ctx.values():
+            for c in cs:
+                c.set_potential(pot)
         self._theta = theta.copy()
+
+    def _run(self, worker: int, grad: bool):
+        """Configurations worker, worker + workers, ... on that worker's
+        contexts: {index: (loss, gradient)}."""
+        out = {}
+        for k in range(worker, len(self.refs), self.workers):
+            pos, _ = self.problem.configs[k]
+            e_ref, f_ref = self.refs[k]
+            ctx = self._ctx[pos.shape[0]][worker]
+            ctx.set_state(pos, None, 0)
+            out[k] = ctx.force_match(f_ref, e_ref, self.w, grad=grad)
+        return out
 
     def evaluate(self, theta, grad: bool = True):
         """(L, dL/dtheta or None)."""
         self._set_theta(theta)
+        if self._pool is None:
+            parts = [self._run(0, grad)]
+        else:
+            parts = list(self._pool.map(lambda wk: self._run(wk, grad), range(self.workers)))
+        results = {}
+        for p in parts:
+            results.update(p)
         total = 0.0
         g = np.zeros(sum(self.sizes)) if grad else None
-        for (pos, _), (e_ref, f_ref) in zip(self.problem.configs, self.refs):
-            ctx = self._ctx[pos.shape[0]]
-            ctx.set_state(pos, None, 0)
-            loss, gc = ctx.force_match(f_ref, e_ref, self.w, grad=grad)
+        for k in range(len(self.refs)):  # configuration order
+            loss, gc = results[k]
             total += loss
             if grad:
                 g += gc
         return total, g
 
     def close(self):
-        for c in self._ctx.values():
-            c.close()
+        if self._pool is not None:
+            self._pool.shutdown()
+            self._pool = None
+        for cs in self._ctx.values():
+            for c in cs:
+                c.close()
         self._ctx = {}
 
 

@@ -139,13 +139,17 @@ __global__ void k_adj_rho(Bufs<double> B, Geom G, int n, int ld, AdjDesc D, int 
     (void)off_F;
 }
 
-// Contributions of one warp's atoms to the coefficient bins, in lane order.
-// Block = one warp; bins in dynamic shared memory (4 * nrows doubles).
+// Contributions of 32 atoms to the coefficient bins.  Block = kAdjWarps
+// warps over the same 32 atoms: warp w takes list columns w, w + kAdjWarps,
+// ... (and warp 0 the F rows), each into bins of its own in dynamic shared
+// memory (4 * nrows doubles per warp), added in column then lane order; the
+// block writes its warps' bins in warp order.
 __global__ void k_adj_accum(Bufs<double> B, Geom G, int n, int ld, AdjDesc D, int off_f, int off_F, const double *g,
                             const double *rho_in, const double *drho_in, double *block_bins)
 {
-    extern __shared__ double bins[];
-    const int lane = threadIdx.x;
+    extern __shared__ double bins_all[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *bins = bins_all + (size_t)warp * 4 * D.nrows;
     for (int r = lane; r < 4 * D.nrows; r += 32) bins[r] = 0.0;
     double h[3];
     load_h<double>(G, h);
@@ -165,11 +169,13 @@ __global__ void k_adj_accum(Bufs<double> B, Geom G, int n, int ld, AdjDesc D, in
         gx = g[p]; gy = g[(size_t)n + p]; gz = g[2 * (size_t)n + p];
         drho = drho_in[p];
         adj_eval(B.coef, off_F, D, 2, rho_in[p], dF, d2F);
-        // F row of rho_p
-        double bv[4], bd[4];
-        row_a = adj_rows(D, 2, rho_in[p], bv, bd);
+        // F row of rho_p (warp 0)
+        if (warp == 0) {
+            double bv[4], bd[4];
+            row_a = adj_rows(D, 2, rho_in[p], bv, bd);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) contrib[c] = D.A * bv[c] - 2.0 * D.w * bd[c] * drho;
+            for (int c = 0; c < 4; ++c) contrib[c] = D.A * bv[c] - 2.0 * D.w * bd[c] * drho;
+        }
     }
     for (int L = 0; L < 32; ++L) {
         if (lane == L && row_a >= 0)
@@ -179,7 +185,7 @@ __global__ void k_adj_accum(Bufs<double> B, Geom G, int n, int ld, AdjDesc D, in
     }
     int kmax = nn;
     for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-    for (int k = 0; k < kmax; ++k) {
+    for (int k = warp; k < kmax; k += kAdjWarps) {
         row_a = row_b = -1;
         if (active && k < nn) {
             uint32_t e = B.list[(size_t)k * ld + p];
@@ -211,7 +217,8 @@ __global__ void k_adj_accum(Bufs<double> B, Geom G, int n, int ld, AdjDesc D, in
             __syncwarp();
         }
     }
-    for (int r = lane; r < 4 * D.nrows; r += 32) block_bins[(size_t)blockIdx.x * 4 * D.nrows + r] = bins[r];
+    for (int r = lane; r < 4 * D.nrows; r += 32)
+        block_bins[((size_t)blockIdx.x * kAdjWarps + warp) * 4 * D.nrows + r] = bins[r];
 }
 
 // Sum the block bins in block order (one thread per coefficient), and the
@@ -267,12 +274,15 @@ int launch_adjoint(const Bufs<double> &B, const Geom &G, const Launch &L, const 
     const int n = L.n;
     const int nb = blocks_for(n, 256);
     k_adj_g<<<nb, 256, 0, L.stream>>>(B, a.f_ref, a.g, n, a.partials_g);
-    k_adj_rho<<<nb, 256, 0, L.stream>>>(B, G, n, L.ld, D, a.off_f, a.off_F, a.g, a.rho, a.drho);
+    // one warp per block: the few atoms of a force-matching configuration
+    // spread over as many SMs' FP64 pipes as they can fill
+    k_adj_rho<<<blocks_for(n, 32), 32, 0, L.stream>>>(B, G, n, L.ld, D, a.off_f, a.off_F, a.g, a.rho, a.drho);
     const int nw = blocks_for(n, 32);
-    const size_t smem = sizeof(double) * 4 * (size_t)D.nrows;
-    k_adj_accum<<<nw, 32, smem, L.stream>>>(B, G, n, L.ld, D, a.off_f, a.off_F, a.g, a.rho, a.drho, a.block_bins);
-    k_adj_finish<<<blocks_for(4 * D.nrows, 256), 256, 0, L.stream>>>(a.block_bins, nw, D.nrows, a.partials_g,
-                                                                      nb, a.coef_grad, a.sq);
+    const size_t smem = adjoint_smem_bytes(D.nrows);
+    k_adj_accum<<<nw, 32 * kAdjWarps, smem, L.stream>>>(B, G, n, L.ld, D, a.off_f, a.off_F, a.g, a.rho, a.drho,
+                                                        a.block_bins);
+    k_adj_finish<<<blocks_for(4 * D.nrows, 256), 256, 0, L.stream>>>(a.block_bins, nw * kAdjWarps, D.nrows,
+                                                                      a.partials_g, nb, a.coef_grad, a.sq);
     int launched = 4;
     if (a.knot_grad) {
         k_adj_knots<<<blocks_for(a.nknots_total, 128), 128, 0, L.stream>>>(
@@ -282,6 +292,11 @@ int launch_adjoint(const Bufs<double> &B, const Geom &G, const Launch &L, const 
     return launched;
 }
 
-size_t adjoint_smem_bytes(int nrows) { return sizeof(double) * 4 * (size_t)nrows; }
+size_t adjoint_smem_bytes(int nrows) { return sizeof(double) * 4 * (size_t)nrows * kAdjWarps; }
+
+cudaError_t allow_adjoint_smem(size_t bytes)
+{
+    return cudaFuncSetAttribute(k_adj_accum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 }  // namespace eammd

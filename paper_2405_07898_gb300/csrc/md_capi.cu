@@ -923,6 +923,7 @@ md_status adjoint_setup(md_ctx *ctx)
         nknots += sp->n;
     }
     if (adjoint_smem_bytes(nrows) > 200 * 1024) return ctx->fail(MD_ERR_CAPACITY, "too many spline intervals for the adjoint bins");
+    CK(allow_adjoint_smem(adjoint_smem_bytes(nrows)));
     std::vector<double> Mt;
     std::vector<int> knot_func, coef0(3), ncoef(3);
     std::vector<long long> mt0;
@@ -949,7 +950,7 @@ md_status adjoint_setup(md_ctx *ctx)
     }
     const int nw = (int)((n + 31) / 32), nb = (int)((n + 255) / 256);
     bool ok = alloc_n(ctx, ctx->adj_g, 3 * n) && alloc_n(ctx, ctx->adj_rho, n) && alloc_n(ctx, ctx->adj_drho, n) &&
-              alloc_n(ctx, ctx->adj_bins, (size_t)nw * 4 * nrows) && alloc_n(ctx, ctx->adj_pg, (size_t)nb) &&
+              alloc_n(ctx, ctx->adj_bins, (size_t)nw * kAdjWarps * 4 * nrows) && alloc_n(ctx, ctx->adj_pg, (size_t)nb) &&
               alloc_n(ctx, ctx->adj_cg, (size_t)4 * nrows) && alloc_n(ctx, ctx->adj_sq, 1) &&
               alloc_n(ctx, ctx->adj_Mt, Mt.size()) && alloc_n(ctx, ctx->adj_kg, (size_t)nknots) &&
               alloc_n(ctx, ctx->adj_knot_func, (size_t)nknots) && alloc_n(ctx, ctx->adj_func_coef0, 3) &&
@@ -1215,6 +1216,16 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     L.ld = (int)((n + 31) / 32 * 32);
     L.block = o.block_size;
     L.nblocks = (int)((n + L.block - 1) / L.block);
+    {
+        // the list build of a small system: blocks as small as it takes to
+        // give every SM two (down to one warp)
+        int dev = 0, nsm = 152;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            nsm = 152;
+        L.list_block = L.block;
+        while (L.list_block > 32 && (n + L.list_block - 1) / L.list_block < 2 * (int64_t)nsm) L.list_block /= 2;
+        L.list_block = std::max(32, L.list_block / 32 * 32);
+    }
     L.nrows = G.ncell[1] * G.ncell[2];
     L.pstride = std::max({1, blocks_for_host(8 * n, std::min(L.block, 128)), L.nrows});
     {

@@ -143,6 +143,7 @@ struct Launch {
     int ld;         // list leading dimension (multiple of 32)
     int cap;        // list slots per atom
     int block;      // threads per block of per-atom kernels
+    int list_block; // threads per block of the list build (smaller for small systems, to fill the SMs)
     int block_d;    // threads per block of the density pass
     int block_f;    // threads per block of the force pass
     int nblocks;    // ceil(n / block)
@@ -248,5 +249,9 @@ struct AdjointArgs {
 
 int launch_adjoint(const Bufs<double> &B, const Geom &G, const Launch &L, const AdjointArgs &a);
 size_t adjoint_smem_bytes(int nrows);
+// Permits `bytes` of dynamic shared memory to the adjoint accumulation.
+cudaError_t allow_adjoint_smem(size_t bytes);
+// Warps that share the 32 atoms of one block of the adjoint accumulation.
+constexpr int kAdjWarps = 4;
 
 }  // namespace eammd

@@ -235,7 +235,7 @@ int launch_rebuild(const Bufs<R> &B, const Geom &G, const Launch &L)
     k_cell_sort<R><<<blocks_for(G.ncells, 256), 256, 0, L.stream>>>(B, G.ncells);
     k_permute<R><<<nb, b, 0, L.stream>>>(B, G, L.n);
     k_rebuild_finish<R><<<1, 1, 0, L.stream>>>(B, L.use_cond);
-    k_build_list<R><<<nb, b, 0, L.stream>>>(B, G, L.n, L.ld, L.cap);
+    k_build_list<R><<<blocks_for(L.n, L.list_block), L.list_block, 0, L.stream>>>(B, G, L.n, L.ld, L.cap);
     return 8;
 }
 

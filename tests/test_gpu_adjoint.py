@@ -115,3 +115,20 @@ def test_set_potential_keeps_grids():
         md.set_potential(p2)
         _, _, F, _, _ = O.eam_eval(O.Potential(p2), O.wrap(s.pos, s.box), s.box, s.types)
         assert rel(md.forces(), F) < 1e-10
+
+
+def test_worker_threads_give_the_same_loss_and_gradient():
+    """Configurations spread over worker contexts (own streams, host
+    threads) and summed in configuration order: loss and gradient bitwise
+    those of one context."""
+    prob = I.fit_problem(n_configs=7, cells=(6, 6, 6), n_knots=24, w=0.1, seed=23)
+    theta = prob.theta0 * (1.0 + 0.01 * np.sin(np.arange(len(prob.theta0))))
+    out = []
+    for workers in (1, 3):
+        fm = autodiff.ForceMatch(prob, workers=workers)
+        out.append(fm.evaluate(theta, grad=True))
+        out.append(fm.evaluate(prob.theta0, grad=True))
+        fm.close()
+    assert out[0][0] == out[2][0] and out[1][0] == out[3][0]
+    np.testing.assert_array_equal(out[0][1], out[2][1])
+    np.testing.assert_array_equal(out[1][1], out[3][1])
