@@ -251,7 +251,8 @@ def run_ours(args):
                       "lanes_density": st["lanes_density"], "lanes_force": st["lanes_force"],
                       "rows_density": st["rows_density"], "rows_force": st["rows_force"],
                       "tiles_density": st["tiles_density"], "tiles_force": st["tiles_force"],
-                      "table_density": st["table_density"], "table_force": st["table_force"]},
+                      "table_density": st["table_density"], "table_force": st["table_force"],
+                      "threads_density": st["threads_density"], "threads_force": st["threads_force"]},
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu

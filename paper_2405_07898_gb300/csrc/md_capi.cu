@@ -705,8 +705,8 @@ md_status reevaluate(md_ctx *ctx)
 }
 
 // Schedule of the density and force passes: time, on the current state
-// (density, and forces without integration; neither changes positions or
-// velocities), the atom-parallel passes with 1, 2, 4, 8 lanes per atom
+// (density, and the force pass with its kicks and drift at dt = 0; neither
+// changes positions or velocities), the atom-parallel passes with 1, 2, 4, 8 lanes per atom
 // gathering the list from device memory, and, on the one-type path, with 1,
 // 2, 4 lanes from a shared-memory list tile and row-staged with 1, 2, 4
 // (where a stage was sized); keep the fastest of each pass.
@@ -754,11 +754,19 @@ md_status autotune(md_ctx *ctx)
     // alike); each candidate keeps its fastest single launch
     std::vector<float> best_d(nc, 1e30f), best_f(nc, 1e30f);
     const int rounds = 6;
+    // the force pass is timed as md_step runs it (kicks and drift fused), at
+    // dt = 0: positions and velocities keep their values; the device state
+    // words it touches are restored afterwards
+    DevState saved;
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(&saved, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost));
     for (int round = 0; round < rounds; ++round) {
         for (int ci = 0; ci < nc; ++ci) {
             set_sched(ctx, cand[ci], cand[ci]);
             Launch L = ctx->L;
             L.use_cond = 0;
+            L.dt = 0.0;
+            for (int t = 0; t < ctx->ntypes; ++t) L.half_kick[t] = 0.0;
             float ms = 0;
             CK(cudaEventRecord(e0, ctx->stream));
             launch_density<R>(B, ctx->G, L, false);
@@ -768,7 +776,7 @@ md_status autotune(md_ctx *ctx)
             CK(cudaEventElapsedTime(&ms, e0, e1));
             if (round > 0) best_d[ci] = std::min(best_d[ci], ms);
             CK(cudaEventRecord(e0, ctx->stream));
-            launch_force<R>(B, ctx->G, L, MODE_MEASURE, false);
+            launch_force<R>(B, ctx->G, L, MODE_CLOSE_OPEN, false);
             CK(cudaEventRecord(e1, ctx->stream));
             CK(cudaEventSynchronize(e1));
             CK(cudaGetLastError());
@@ -777,6 +785,7 @@ md_status autotune(md_ctx *ctx)
             ctx->fixed_launches += 2;
         }
     }
+    CK(cudaMemcpy(ctx->st, &saved, sizeof(DevState), cudaMemcpyHostToDevice));
     // candidates in order of preference: a later one must win by 3%
     int cd = 0, cf = 0;
     for (int ci = 1; ci < nc; ++ci) {
