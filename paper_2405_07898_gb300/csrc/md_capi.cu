@@ -735,7 +735,7 @@ md_status autotune(md_ctx *ctx)
     // wave of blocks on the GPU
     std::vector<PassSched> cand;
     for (int t : {1, 2})
-        for (int b : {256, 224, 192, 160, 128}) cand.push_back({t, SCHED_ATOMS, b});
+        for (int b : {256, 224, 192, 160, 128, 96, 64}) cand.push_back({t, SCHED_ATOMS, b});
     cand.push_back({4, SCHED_ATOMS, 256});
     cand.push_back({8, SCHED_ATOMS, 256});
     if (!ctx->L.multi) {
