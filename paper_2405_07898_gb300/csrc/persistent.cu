@@ -33,6 +33,13 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
     return v;
 }
 
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(__cvta_generic_to_global(p)) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
 {
     unsigned long long v;
@@ -62,9 +69,13 @@ __device__ __forceinline__ bool grid_barrier(PersistScratch *ps, unsigned *err, 
             const unsigned long long g = gridDim.x;
             const unsigned long long target = (a / g + 1) * g;
             if (a + 1 != target) {
+                // relaxed polls, one acquire load once the count is reached;
+                // the error word and the clock are read every 64th poll only
                 const uint64_t t0 = global_ns();
-                while (ld_acquire(&ps->arrive) < target) {
-                    if ((ld_acquire(err) & ERR_TIMEOUT) || global_ns() - t0 > wait_ns) {
+                unsigned spins = 0;
+                while (ld_relaxed(&ps->arrive) < target || ld_acquire(&ps->arrive) < target) {
+                    if ((++spins & 63u) == 0 &&
+                        ((ld_acquire(err) & ERR_TIMEOUT) || global_ns() - t0 > wait_ns)) {
                         atomicOr(err, ERR_TIMEOUT);
                         good = 0;
                         break;
