@@ -65,7 +65,15 @@ __device__ __forceinline__ void bin_atom(const Bufs<R> &B, const Geom &G, int s,
     if (!finite) atomicOr(&B.st->error, ERR_NONFINITE);
     int cell = (c[2] * G.ncell[1] + c[1]) * G.ncell[0] + c[0];
     B.cell_old[i] = cell;
-    B.slot[i] = atomicAdd(&B.count[cell], 1);
+    // one atomic per distinct cell among the warp's active lanes (atoms in
+    // cell order mostly share cells); the lanes of a cell take consecutive
+    // slots from it in lane order
+    const unsigned peers = __match_any_sync(__activemask(), cell);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&B.count[cell], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    B.slot[i] = base + __popc(peers & ((1u << lane) - 1u));
 }
 
 // Exclusive scan of all cell counts by one block (any size): cell_start[c] =
