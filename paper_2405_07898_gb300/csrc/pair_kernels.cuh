@@ -422,7 +422,7 @@ __device__ __forceinline__ void prefetch_warp_streams(const Bufs<R> &B, const La
 
 // Pairs in flight per lane: the type-dependent path needs more registers a pair.
 template <bool MULTI> struct PairsInFlight {
-    static constexpr int density = MULTI ? 2 : 4;
+    static constexpr int density = MULTI ? 2 : 3;
     static constexpr int force = 2;
 };
 
