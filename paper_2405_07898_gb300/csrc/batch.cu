@@ -28,6 +28,7 @@ namespace eammd {
 namespace {
 
 constexpr int kMaxBatchWarps = 32;  // blocks of up to 1024 threads
+constexpr int kBatchDensityPairs = 4;  // pairs in flight per lane in the density phase (3: 2.09 G atom-steps/s, 4: 2.14 G)
 
 struct RepParam {
     int n;          // atoms
@@ -430,17 +431,18 @@ __device__ void run_replica(const BatchBufs &B, Smem &S, int r, int mode, int ns
             const int nn = B.nnb[P.atom_off + i];
             const uint32_t *lp = B.list + P.list_off + i;
             float rho = 0.f;
-            // four pairs per round, all gathers issued before any is used;
-            // the sum runs in column order
-            for (int k = 0; k < nn; k += 4) {
-                uint32_t e[4];
-                float4 u[4];
+            // kBatchDensityPairs pairs per round, all gathers issued before
+            // any is used; the sum runs in column order
+            constexpr int UQ = kBatchDensityPairs;
+            for (int k = 0; k < nn; k += UQ) {
+                uint32_t e[UQ];
+                float4 u[UQ];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) e[q] = (k + q < nn) ? lp[(size_t)(k + q) * P.ld] : 0u;
+                for (int q = 0; q < UQ; ++q) e[q] = (k + q < nn) ? lp[(size_t)(k + q) * P.ld] : 0u;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) u[q] = sw[(q == 0 || k + q < nn ? e[q] : e[0]) & kIndexMask];
+                for (int q = 0; q < UQ; ++q) u[q] = sw[(q == 0 || k + q < nn ? e[q] : e[0]) & kIndexMask];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < UQ; ++q) {
                     const Shift<float> shf = entry_shift<float>(e[q], hf);
                     const float dx = (u[q].x - ui.x) + shf.x, dy = (u[q].y - ui.y) + shf.y,
                                 dz = (u[q].z - ui.z) + shf.z;
