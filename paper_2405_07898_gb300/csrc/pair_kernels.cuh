@@ -2,9 +2,11 @@
 //
 // Two schedules share the per-atom work:
 //   * atom-parallel (k_density, k_force): TPA lanes cooperate on one atom;
-//     lane l walks list columns l, l+TPA, ... two at a time (both gathers
-//     issued before either is used), the lanes' sums meet by warp shuffles;
-//     neighbour records are gathered from global memory;
+//     lane l walks list columns l, l+TPA, ... a few at a time (every gather
+//     of a round issued before any is used: three pairs a round in the
+//     density pass, two in the force pass with the next round in flight),
+//     the lanes' sums meet by warp shuffles; neighbour records are gathered
+//     from global memory;
 //   * row-staged (k_density_rows, k_force_rows): one block per row of cells
 //     (all cx for a fixed cy, cz) first copies the records of the 3 x 3 rows
 //     around it -- every neighbour its atoms can have -- into shared memory
