@@ -277,9 +277,10 @@ def _timed_steps(md, nsteps, dt, reps=1):
 def run_sweep(args):
     """Strong-scaling sweep: BCC cubes of 1,024 .. 314,928 atoms and the
     799,496-atom box at 1,000 K (mixed precision): timesteps/s of md_step
-    replayed as CUDA graphs and, up to 314,928 atoms, as one cooperative
-    launch per call (the path the library picks automatically up to 65,536
-    atoms)."""
+    replayed as CUDA graphs, up to 314,928 atoms as one cooperative launch per
+    call, and up to 32,768 atoms as one thread-block cluster per call (the
+    library times the two single-launch forms and takes one automatically up
+    to 65,536 atoms)."""
     import torch
     from paper_2405_07898_gb300 import binding, inputs as I
 
@@ -288,19 +289,21 @@ def run_sweep(args):
     for s in I.sweep_systems(temperature=1000.0):
         steps = max(200, min(20000, int(2e8 // s.n) // 10 * 10))
         row = {"atoms": s.n, "steps": steps}
-        for mode in ("off", "on"):
-            if mode == "on" and s.n > 400000:
+        for mode in ("off", "on", "cluster"):
+            if (mode == "on" and s.n > 400000) or (mode == "cluster" and s.n > 32768):
                 continue
             md = binding.MD(s, precision="mixed", persistent=mode)
             md.step(100, DT_FS)
             t = _timed_steps(md, steps, DT_FS)
-            key = "graph" if mode == "off" else "single_launch"
+            key = {"off": "graph", "on": "single_launch", "cluster": "cluster"}[mode]
             row[key + "_ts_per_s"] = steps / t
             row[key + "_atom_steps_per_s"] = s.n * steps / t
-            if mode == "on":
+            if mode != "off":
                 st = md.stats()
-                row["single_launch_blocks"] = st["persistent_blocks"]
-                row["single_launch_lanes"] = st["persistent_lanes"]
+                row[key + "_blocks"] = st["persistent_blocks"]
+                row[key + "_lanes"] = st["persistent_lanes"]
+                if mode == "cluster":
+                    row["cluster_shared_tables"] = int(st["persistent_cluster"] == 2)
             md.close()
         rows.append(row)
     print(json.dumps({"workload": "bcc_sweep_1000K_mixed", "unit": "timesteps/s", "sweep": rows}), flush=True)

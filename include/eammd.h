@@ -82,7 +82,7 @@ typedef struct {
 } md_potential;
 
 enum { MD_PRECISION_FP64 = 0, MD_PRECISION_MIXED = 1 };
-enum { MD_PERSIST_AUTO = 0, MD_PERSIST_OFF = 1, MD_PERSIST_ON = 2 };
+enum { MD_PERSIST_AUTO = 0, MD_PERSIST_OFF = 1, MD_PERSIST_ON = 2, MD_PERSIST_CLUSTER = 3 };
 enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2, MD_SCHEDULE_TILES = 3,
        MD_SCHEDULE_TABLE = 4 };
 
@@ -138,18 +138,25 @@ enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2, MD_SCH
  *                    memory and walk tiles of atoms; lanes_per_atom 1, 2 or
  *                    4; forces bitwise those of MD_SCHEDULE_ATOMS.  Falls
  *                    back to MD_SCHEDULE_ATOMS where it does not apply.
- *   persistent       MD_PERSIST_AUTO (0): md_step runs as one cooperative
- *                    launch (all phases of all steps, blocks meeting at grid
- *                    barriers) for systems of at most 65,536 atoms, else as
- *                    CUDA graphs.  MD_PERSIST_OFF: always the graph (or
- *                    eager) path.  MD_PERSIST_ON: always the single launch.
- *                    Lanes per atom of the single launch: lanes_per_atom, or
- *                    timed at md_create over 1, 2, 4, 8 on steps at dt = 0
- *                    (the state is restored).  Positions, velocities and
- *                    forces are bitwise those of the graph path with the same
- *                    lanes per atom; energy sums differ in rounding only.  A
- *                    grid-barrier wait longer than 1 s ends the launch and
- *                    raises MD_ERR_TIMEOUT.
+ *   persistent       MD_PERSIST_AUTO (0): md_step runs as one launch (all
+ *                    phases of all steps) for systems of at most 65,536
+ *                    atoms, else as CUDA graphs.  The launch takes one of two
+ *                    forms: a cooperative grid of all resident blocks
+ *                    meeting at grid barriers in device memory, or (up to
+ *                    32,768 atoms) one thread-block cluster of at most 16
+ *                    CTAs that hold their atoms' records in shared memory,
+ *                    read neighbours through distributed shared memory and
+ *                    meet at cluster barriers.  MD_PERSIST_OFF: always the
+ *                    graph (or eager) path.  MD_PERSIST_ON: always the
+ *                    cooperative grid.  MD_PERSIST_CLUSTER (3): always the
+ *                    cluster (MD_ERR_CUDA at md_create if the system does
+ *                    not fit one).  Form and lanes per atom: lanes_per_atom,
+ *                    or timed at md_create over 1, 2, 4, 8 and the forms on
+ *                    steps at dt = 0 (the state is restored).  Positions,
+ *                    velocities and forces are bitwise those of the graph
+ *                    path with the same lanes per atom; energy sums differ
+ *                    in rounding only.  A barrier wait longer than 1 s ends
+ *                    the launch and raises MD_ERR_TIMEOUT.
  *   open_axes        one bit per open (non-periodic) axis: 1 = x, 2 = y,
  *                    4 = z; 0 = fully periodic.  The free-surface slabs of
  *                    the paper's benchmarks (Section "How Performance Was
@@ -269,6 +276,7 @@ typedef struct {
     int32_t threads_force;   /* threads per block of the force pass */
     int32_t persistent_blocks; /* blocks of the single-launch md_step (0: graphs) */
     int32_t persistent_lanes;  /* lanes per atom of its pair passes */
+    int32_t persistent_cluster; /* 1: the single launch is one cluster; 2: with the spline rows in shared memory */
 } md_stats_t;
 
 md_status md_stats(md_ctx *ctx, md_stats_t *out);

@@ -24,7 +24,7 @@ STATUS = {0: "MD_OK", -1: "MD_ERR_ARG", -2: "MD_ERR_BOX", -3: "MD_ERR_CUDA", -4:
           -5: "MD_ERR_NONFINITE", -6: "MD_ERR_TIMEOUT", -7: "MD_ERR_LIST_OVERFLOW",
           -8: "MD_ERR_CAPACITY"}
 PRECISION = {"fp64": 0, "mixed": 1}
-PERSIST = {"auto": 0, "off": 1, "on": 2}
+PERSIST = {"auto": 0, "off": 1, "on": 2, "cluster": 3}
 SCHEDULE = {"auto": 0, "atoms": 1, "rows": 2, "tiles": 3, "table": 4}
 
 # every entry point declared in include/eammd.h
@@ -72,7 +72,7 @@ class Stats(C.Structure):
                 ("tiles_force", C.c_int32), ("table_density", C.c_int32),
                 ("table_force", C.c_int32), ("threads_density", C.c_int32),
                 ("threads_force", C.c_int32), ("persistent_blocks", C.c_int32),
-                ("persistent_lanes", C.c_int32)]
+                ("persistent_lanes", C.c_int32), ("persistent_cluster", C.c_int32)]
 
 
 class Profile(C.Structure):

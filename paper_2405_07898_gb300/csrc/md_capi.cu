@@ -100,6 +100,8 @@ struct md_ctx {
     // persistent step launch (md_step as one cooperative kernel)
     PersistScratch *ps = nullptr;
     int persist_tpa = 0, persist_grid = 0;  // 0: graph path
+    int persist_cluster = 0;                // 1: the single launch is one cluster; 2: with shared tables
+    ClusterPlan persist_plan{0, 0};
     std::string err;
 
     md_status fail(md_status s, const std::string &m)
@@ -441,6 +443,12 @@ md_status step_impl(md_ctx *ctx, int64_t nsteps, double dt)
     Launch L = ctx->L;
     L.use_cond = 0;
     L.cond = 0;
+    if (ctx->persist_cluster > 0) {
+        CK(launch_steps_cluster<R>(B, ctx->G, L, nsteps, ctx->persist_tpa, ctx->persist_cluster == 2,
+                                   ctx->persist_plan, ctx->ps));
+        ctx->fixed_launches += 1;
+        return MD_OK;
+    }
     if (ctx->persist_grid > 0) {
         CK(launch_steps<R>(B, ctx->G, L, nsteps, ctx->persist_tpa, ctx->persist_grid, ctx->ps));
         ctx->fixed_launches += 1;
@@ -811,17 +819,23 @@ md_status autotune(md_ctx *ctx)
 // graph replay (measured on GB300 over the BCC sweep).
 constexpr int64_t kPersistentAutoAtoms = 65536;
 
-// The persistent step launch: lanes per atom (from the options, else timed
-// over 1, 2, 4, 8 on rebuild_every - 1 steps at dt = 0, which moves no atom
-// and builds no list; the device state is restored after each trial) and the
-// resident grid.
+// The persistent step launch.  Forms: a cooperative grid of as many blocks as
+// are resident (any size), or one thread-block cluster whose CTAs keep their
+// atoms' records in shared memory (up to kMaxClusterCtas << kMaxClusterShift
+// atoms), optionally with the FP32 spline rows there too.  Lanes per atom come
+// from the options, else every feasible (form, lanes) pair is timed over
+// rebuild_every - 1 steps at dt = 0, which moves no atom and builds no list;
+// the device state is restored after each trial.
 template <class R>
 md_status setup_persistent(md_ctx *ctx)
 {
     ctx->persist_grid = 0;
+    ctx->persist_cluster = 0;
     const md_options &o = ctx->opt;
-    const bool want = o.persistent == MD_PERSIST_ON || (o.persistent == MD_PERSIST_AUTO && ctx->n <= kPersistentAutoAtoms);
+    const bool want = o.persistent == MD_PERSIST_ON || o.persistent == MD_PERSIST_CLUSTER ||
+                      (o.persistent == MD_PERSIST_AUTO && ctx->n <= kPersistentAutoAtoms);
     if (!want || ctx->n == 0) return MD_OK;
+    const bool forced = o.persistent != MD_PERSIST_AUTO;
     if (!ctx->ps) {
         if (!alloc_n(ctx, ctx->ps, 1)) return ctx->fail(MD_ERR_OOM, "device allocation failed");
         CK(cudaMemsetAsync(ctx->ps, 0, sizeof(PersistScratch), ctx->stream));
@@ -829,20 +843,43 @@ md_status setup_persistent(md_ctx *ctx)
     int dev = 0, coop = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-    if (!coop) {
-        if (o.persistent == MD_PERSIST_ON) return ctx->fail(MD_ERR_CUDA, "the device has no cooperative launch");
+    const Bufs<R> &B = bufs<R>(ctx);
+    std::vector<int> tpas;
+    if (o.lanes_per_atom > 0) tpas.push_back(o.lanes_per_atom);
+    else if (ctx->L.rebuild_every < 2) tpas.push_back(2);  // every step builds: no state-neutral trial
+    else tpas = {1, 2, 4, 8};
+    struct Cand {
+        int tpa, grid, cluster;
+        ClusterPlan plan;
+    };
+    std::vector<Cand> cand;
+    for (int tpa : tpas) {
+        if (o.persistent != MD_PERSIST_CLUSTER && coop) {
+            const int grid = persistent_grid<R>(ctx->L, tpa);
+            if (grid > 0) cand.push_back({tpa, grid, 0, {0, 0}});
+        }
+        if (o.persistent != MD_PERSIST_ON) {
+            // schedule ATOMS: records only in shared memory; TABLE: the
+            // spline rows too; otherwise both are timed
+            const int f0 = o.schedule == MD_SCHEDULE_TABLE ? 2 : 1, f1 = o.schedule == MD_SCHEDULE_ATOMS ? 1 : 2;
+            for (int form = f0; form <= f1; ++form) {
+                ClusterPlan plan{0, 0};
+                if (cluster_plan<R>(ctx->L, tpa, form == 2, plan)) cand.push_back({tpa, plan.nct, form, plan});
+            }
+        }
+    }
+    if (cand.empty()) {
+        if (forced) return ctx->fail(MD_ERR_CUDA, "the persistent step kernel cannot be resident");
         return MD_OK;
     }
-    const Bufs<R> &B = bufs<R>(ctx);
-    std::vector<int> cand;
-    if (o.lanes_per_atom > 0) cand.push_back(o.lanes_per_atom);
-    else if (ctx->L.rebuild_every < 2) cand.push_back(2);  // every step builds: no state-neutral trial
-    else cand = {1, 2, 4, 8};
-    if (cand.size() == 1) {
-        ctx->persist_tpa = cand[0];
-        ctx->persist_grid = persistent_grid<R>(ctx->L, cand[0]);
-        if (ctx->persist_grid <= 0 && o.persistent == MD_PERSIST_ON)
-            return ctx->fail(MD_ERR_CUDA, "the persistent step kernel cannot be resident");
+    auto take = [&](const Cand &c) {
+        ctx->persist_tpa = c.tpa;
+        ctx->persist_cluster = c.cluster;
+        ctx->persist_plan = c.plan;
+        ctx->persist_grid = c.cluster ? 0 : c.grid;
+    };
+    if (cand.size() == 1 || ctx->L.rebuild_every < 2) {
+        take(cand[0]);
         return MD_OK;
     }
     const int trial_steps = ctx->L.rebuild_every - 1;
@@ -856,36 +893,30 @@ md_status setup_persistent(md_ctx *ctx)
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_tpa = 0, best_grid = 0;
-    for (int round = 0; round < (cand.size() > 1 ? 3 : 1); ++round) {
-        for (int tpa : cand) {
-            const int grid = persistent_grid<R>(ctx->L, tpa);
-            if (grid <= 0) continue;
+    int best_i = -1;
+    for (int round = 0; round < 3; ++round) {
+        for (size_t c = 0; c < cand.size(); ++c) {
+            const Cand &k = cand[c];
             CK(cudaEventRecord(e0, ctx->stream));
-            CK(launch_steps<R>(B, ctx->G, L, trial_steps, tpa, grid, ctx->ps));
+            if (k.cluster) CK(launch_steps_cluster<R>(B, ctx->G, L, trial_steps, k.tpa, k.cluster == 2, k.plan, ctx->ps));
+            else CK(launch_steps<R>(B, ctx->G, L, trial_steps, k.tpa, k.grid, ctx->ps));
             CK(cudaEventRecord(e1, ctx->stream));
             CK(cudaEventSynchronize(e1));
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, e0, e1));
             CK(cudaMemcpy(ctx->st, &saved, sizeof(DevState), cudaMemcpyHostToDevice));
             ctx->fixed_launches += 1;
-            // a wider schedule must win by 3%
+            // a later candidate must win by 3%
             if (ms < 0.97f * best) {
                 best = ms;
-                best_tpa = tpa;
-                best_grid = grid;
+                best_i = (int)c;
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (saved.error) return check_device_errors(ctx);
-    if (best_grid <= 0) {
-        if (o.persistent == MD_PERSIST_ON) return ctx->fail(MD_ERR_CUDA, "the persistent step kernel cannot be resident");
-        return MD_OK;
-    }
-    ctx->persist_tpa = best_tpa;
-    ctx->persist_grid = best_grid;
+    take(cand[best_i]);
     return check_device_errors(ctx);
 }
 
@@ -1166,8 +1197,8 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     if (o.schedule >= MD_SCHEDULE_ROWS && o.lanes_per_atom == 8)
         return bad(MD_ERR_ARG, "row-staged, list-tiled and shared-table passes take 1, 2 or 4 lanes per atom");
     if (o.stage_capacity < 0) return bad(MD_ERR_ARG, "stage_capacity must be >= 0");
-    if (o.persistent < MD_PERSIST_AUTO || o.persistent > MD_PERSIST_ON)
-        return bad(MD_ERR_ARG, "persistent must be MD_PERSIST_AUTO, _OFF or _ON");
+    if (o.persistent < MD_PERSIST_AUTO || o.persistent > MD_PERSIST_CLUSTER)
+        return bad(MD_ERR_ARG, "persistent must be MD_PERSIST_AUTO, _OFF, _ON or _CLUSTER");
     if (o.wait_limit_us < 0) return bad(MD_ERR_ARG, "wait_limit_us must be >= 0");
 
     md_ctx *ctx = new (std::nothrow) md_ctx();
@@ -1428,8 +1459,9 @@ md_status md_stats(md_ctx *ctx, md_stats_t *out)
     out->table_force = ctx->L.tab_f;
     out->threads_density = ctx->L.block_d;
     out->threads_force = ctx->L.block_f;
-    out->persistent_blocks = ctx->persist_grid;
-    out->persistent_lanes = ctx->persist_tpa;
+    out->persistent_blocks = ctx->persist_cluster ? ctx->persist_plan.nct : ctx->persist_grid;
+    out->persistent_lanes = (ctx->persist_cluster || ctx->persist_grid) ? ctx->persist_tpa : 0;
+    out->persistent_cluster = ctx->persist_cluster;
     out->stage_capacity = ctx->L.stage_cap;
     return MD_OK;
 }

@@ -93,7 +93,7 @@ def test_create_rejects_out_of_range_enums():
     pos = np.ascontiguousarray(s.pos, dtype=np.float64)
     types = np.ascontiguousarray(s.types, dtype=np.int32)
     dp = ctypes.POINTER(ctypes.c_double)
-    for field, value in (("schedule", 5), ("persistent", 3), ("precision", 2)):
+    for field, value in (("schedule", 5), ("persistent", 4), ("precision", 2)):
         opt = binding.Options()
         lib.md_options_default(ctypes.byref(opt))
         setattr(opt, field, value)

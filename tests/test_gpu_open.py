@@ -95,19 +95,20 @@ def test_open_trajectory_fp64_matches_oracle():
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_open_schedules_and_single_launch_bitwise(precision):
     """Row staging must drop rows beyond open y/z edges; tiles, the shared
-    table and the single launch follow the same lists."""
+    table and both forms of the single launch follow the same lists."""
     s = I.bcc_slab_small(7)
     out = {}
     for name, kw in (("atoms", dict(schedule="atoms", persistent="off")),
                      ("rows", dict(schedule="rows", persistent="off")),
                      ("tiles", dict(schedule="tiles", persistent="off")),
                      ("table", dict(schedule="table", persistent="off")),
-                     ("single", dict(schedule="atoms", persistent="on"))):
+                     ("single", dict(schedule="atoms", persistent="on")),
+                     ("cluster", dict(schedule="atoms", persistent="cluster"))):
         with binding.MD(s, precision=precision, lanes_per_atom=2, **kw) as md:
             f0 = md.forces()
             md.step(30, 2.0)
             out[name] = (f0, md.get_state()[0], md.forces())
-    for name in ("rows", "tiles", "table", "single"):
+    for name in ("rows", "tiles", "table", "single", "cluster"):
         for a, b in zip(out[name], out["atoms"]):
             np.testing.assert_array_equal(a, b)
     _, _, F, _, _ = oracle_eval(s, out["atoms"][1])
