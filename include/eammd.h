@@ -142,11 +142,13 @@ enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2, MD_SCH
  *                    phases of all steps) for systems of at most 65,536
  *                    atoms, else as CUDA graphs.  The launch takes one of two
  *                    forms: a cooperative grid of all resident blocks
- *                    meeting at grid barriers in device memory, or (up to
- *                    32,768 atoms) one thread-block cluster of at most 16
- *                    CTAs that hold their atoms' records in shared memory,
- *                    read neighbours through distributed shared memory and
- *                    meet at cluster barriers.  MD_PERSIST_OFF: always the
+ *                    meeting at grid barriers in device memory, or (a few
+ *                    thousand atoms: as many as the shared memory of 16 CTAs
+ *                    holds) one thread-block cluster of at most 16 CTAs that
+ *                    keep their atoms' state and lists in shared memory
+ *                    between list builds, read neighbours through
+ *                    distributed shared memory and meet at cluster
+ *                    barriers.  MD_PERSIST_OFF: always the
  *                    graph (or eager) path.  MD_PERSIST_ON: always the
  *                    cooperative grid.  MD_PERSIST_CLUSTER (3): always the
  *                    cluster (MD_ERR_CUDA at md_create if the system does

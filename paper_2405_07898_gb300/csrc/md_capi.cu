@@ -3,6 +3,7 @@
 // whose list rebuild sits in a device-side conditional node), and the
 // marshalling of states between the caller's order and the sorted order.
 #include "eammd.h"
+#include "cluster.cuh"
 #include "md_internal.cuh"
 #include "spline_host.h"
 
@@ -101,7 +102,8 @@ struct md_ctx {
     PersistScratch *ps = nullptr;
     int persist_tpa = 0, persist_grid = 0;  // 0: graph path
     int persist_cluster = 0;                // 1: the single launch is one cluster; 2: with shared tables
-    ClusterPlan persist_plan{0, 0};
+    ClusterPlan persist_plan{0, 0, 0};
+    int persist_cap = 0;                    // list capacity the cluster plan was made for
     std::string err;
 
     md_status fail(md_status s, const std::string &m)
@@ -434,9 +436,17 @@ md_status get_graph(md_ctx *ctx, int kind, int nsteps, double dt, cudaGraphExec_
     return MD_OK;
 }
 
+template <class R> md_status setup_persistent(md_ctx *ctx);
+
 template <class R>
 md_status step_impl(md_ctx *ctx, int64_t nsteps, double dt)
 {
+    // the cluster form holds the list columns in shared memory: a capacity
+    // grown since it was planned (by md_set_state) needs a new plan
+    if (ctx->persist_cluster > 0 && ctx->persist_cap != ctx->L.cap) {
+        md_status rc = setup_persistent<R>(ctx);
+        if (rc != MD_OK) return rc;
+    }
     const Bufs<R> &B = bufs<R>(ctx);
     ctx->L.dt = dt;
     for (int t = 0; t < ctx->ntypes; ++t) ctx->L.half_kick[t] = 0.5 * dt * kAccel / ctx->mass[t];
@@ -821,8 +831,8 @@ constexpr int64_t kPersistentAutoAtoms = 65536;
 
 // The persistent step launch.  Forms: a cooperative grid of as many blocks as
 // are resident (any size), or one thread-block cluster whose CTAs keep their
-// atoms' records in shared memory (up to kMaxClusterCtas << kMaxClusterShift
-// atoms), optionally with the FP32 spline rows there too.  Lanes per atom come
+// atoms' state and lists in shared memory (as many atoms as kMaxClusterCtas
+// CTAs hold), optionally with the FP32 spline rows there too.  Lanes per atom come
 // from the options, else every feasible (form, lanes) pair is timed over
 // rebuild_every - 1 steps at dt = 0, which moves no atom and builds no list;
 // the device state is restored after each trial.
@@ -856,15 +866,16 @@ md_status setup_persistent(md_ctx *ctx)
     for (int tpa : tpas) {
         if (o.persistent != MD_PERSIST_CLUSTER && coop) {
             const int grid = persistent_grid<R>(ctx->L, tpa);
-            if (grid > 0) cand.push_back({tpa, grid, 0, {0, 0}});
+            if (grid > 0) cand.push_back({tpa, grid, 0, {0, 0, 0}});
         }
         if (o.persistent != MD_PERSIST_ON) {
             // schedule ATOMS: records only in shared memory; TABLE: the
             // spline rows too; otherwise both are timed
             const int f0 = o.schedule == MD_SCHEDULE_TABLE ? 2 : 1, f1 = o.schedule == MD_SCHEDULE_ATOMS ? 1 : 2;
             for (int form = f0; form <= f1; ++form) {
-                ClusterPlan plan{0, 0};
-                if (cluster_plan<R>(ctx->L, tpa, form == 2, plan)) cand.push_back({tpa, plan.nct, form, plan});
+                ClusterPlan plan{0, 0, 0};
+                const int nF = ctx->shapes.empty() ? 0 : ctx->shapes[0].n - 1;  // F of type 0
+                if (cluster_plan<R>(ctx->L, tpa, form == 2, nF, plan)) cand.push_back({tpa, plan.nct, form, plan});
             }
         }
     }
@@ -876,6 +887,7 @@ md_status setup_persistent(md_ctx *ctx)
         ctx->persist_tpa = c.tpa;
         ctx->persist_cluster = c.cluster;
         ctx->persist_plan = c.plan;
+        ctx->persist_cap = ctx->L.cap;
         ctx->persist_grid = c.cluster ? 0 : c.grid;
     };
     if (cand.size() == 1 || ctx->L.rebuild_every < 2) {

@@ -183,13 +183,6 @@ struct PersistScratch {
     unsigned maxdisp[2];
 };
 constexpr int kPersistentBlock = 256;
-constexpr int kMaxClusterCtas = 16;   // CTAs of the cluster form of the single launch (a non-portable size)
-constexpr int kMaxClusterShift = 11;  // at most 2^11 atoms per CTA in the cluster form
-
-// The cluster form: CTA r owns atoms [r 2^shift, (r + 1) 2^shift), nct CTAs.
-struct ClusterPlan {
-    int shift, nct;
-};
 
 // Host-side launchers (rebuild.cu, pair_f32.cu, pair_f64.cu, persistent.cu).  All are asynchronous on L.stream and
 // return the number of kernels queued.
@@ -205,14 +198,6 @@ template <class R> int persistent_grid(const Launch &L, int tpa);
 template <class R>
 cudaError_t launch_steps(const Bufs<R> &B, const Geom &G, const Launch &L, long long nsteps, int tpa, int grid,
                          PersistScratch *ps);
-// md_step as one launch of a single thread-block cluster whose CTAs hold
-// their atoms' records in shared memory (persistent.cu); tabsm: the FP32
-// fused spline rows in shared memory too.  cluster_plan: the fewest atoms per
-// CTA with which the system fits a resident cluster (false if none).
-template <class R> bool cluster_plan(const Launch &L, int tpa, bool tabsm, ClusterPlan &plan);
-template <class R>
-cudaError_t launch_steps_cluster(const Bufs<R> &B, const Geom &G, const Launch &L, long long nsteps, int tpa,
-                                 bool tabsm, const ClusterPlan &plan, PersistScratch *ps);
 
 // Opt the row-staged and list-tiled passes in to `bytes` of dynamic shared
 // memory.

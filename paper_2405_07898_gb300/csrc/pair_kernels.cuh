@@ -236,15 +236,13 @@ __device__ __forceinline__ R density_lane(const Bufs<R> &B, const R (&h)[3], R r
 
 // F'(rho_i) into the atom's record (w word) and F(rho_i) for the energy.
 template <class R>
-__device__ __forceinline__ R embed(const Bufs<R> &B, typename V4<R>::T *sw, int i, int ti, R rho,
-                                   typename V4<R>::T *mirror = nullptr)
+__device__ __forceinline__ R embed(const Bufs<R> &B, typename V4<R>::T *sw, int i, int ti, R rho)
 {
     const Tables<R> &T = *B.tables;
     R Fv, Fd;
     if (spline_any(T.F[ti], B.coef, rho, Fv, Fd)) atomicAdd(&B.st->table_oor, 1ull);
     // the force pass reads w with the coordinates; the density pass never does
     reinterpret_cast<R *>(sw + i)[3] = Fd;
-    if (mirror) reinterpret_cast<R *>(mirror)[3] = Fd;
     return Fv;
 }
 
@@ -337,12 +335,10 @@ __device__ __forceinline__ void force_lane(const Bufs<R> &B, const Launch &L, co
 // ... < 3) once the lanes' forces are summed: MODE_CLOSE* applies the closing
 // half kick v += F dt/(2m); MODE_CLOSE_OPEN also the next step's opening
 // half kick and the drift x += v dt, writing the next record and the
-// displacement since the last list build; MODE_MEASURE only stores F.  A
-// non-null mirror gets the coordinates of the next record as well.
+// displacement since the last list build; MODE_MEASURE only stores F.
 template <class R, int MODE, bool ENERGY, int TPA>
 __device__ __forceinline__ void integrate(const Bufs<R> &B, const Launch &L, int s, int sp, int i, int l, int ti,
-                                          const R (&f)[3], double &ke, float &d2,
-                                          typename V4<R>::T *mirror = nullptr)
+                                          const R (&f)[3], double &ke, float &d2)
 {
     if (l == 0 && !isfinite(f[0] + f[1] + f[2])) atomicOr(&B.st->error, ERR_NONFINITE);
     const double kq = L.half_kick[ti];
@@ -364,9 +360,7 @@ __device__ __forceinline__ void integrate(const Bufs<R> &B, const Launch &L, int
         if (MODE == MODE_CLOSE_OPEN) {
             const double dn = fma(v, L.dt, B.d[c][i]);
             B.d[c][i] = dn;
-            const R uc = B.uref[c][i] + (R)dn;
-            reinterpret_cast<R *>(B.shadow[sp ^ 1] + i)[c] = uc;
-            if (mirror) reinterpret_cast<R *>(mirror)[c] = uc;
+            reinterpret_cast<R *>(B.shadow[sp ^ 1] + i)[c] = B.uref[c][i] + (R)dn;
             const float gc = (float)dn;
             d2 += gc * gc;
         }

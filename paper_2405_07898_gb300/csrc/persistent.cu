@@ -13,6 +13,7 @@
 // ERR_TIMEOUT and every later barrier of the launch returns at once, so the
 // kernel ends within about the limit of a stuck block and the host reports
 // MD_ERR_TIMEOUT.
+#include "cluster.cuh"
 #include "pair_kernels.cuh"
 #include "rebuild_device.cuh"
 
@@ -248,14 +249,19 @@ __global__ void __launch_bounds__(256) k_steps(Bufs<R> B, Geom G, Launch L, long
 // ---- the same step loop in one thread-block cluster ----
 //
 // Up to a few thousand atoms a step is a few microseconds of latency-bound
-// work, and a grid barrier (a device-memory round trip, across both dies, for
-// the arrival and again for the release) is a large part of it; so is every
-// neighbour record fetched from L2 after the barrier's acquire.  Here the
-// step loop runs in one cluster of at most 16 CTAs:
-//   * CTA r owns the atoms [r 2^shift, (r + 1) 2^shift) and holds both record
-//     buffers of its atoms in shared memory, written wherever shadow[] is
-//     (which is still kept for the other entry points); neighbour records are
-//     read from their owner's copy through distributed shared memory;
+// work.  In the cooperative grid every barrier is a device-memory round trip
+// (arrival and release) whose release also waits for the block's stores to
+// reach L2, and after its acquire every list column, count and neighbour
+// record comes from L2 again.  Here the step loop runs in one cluster of at
+// most 16 CTAs and, between list builds, touches device memory only for the
+// embedding-function rows:
+//   * CTA r owns the atoms [r 2^shift, (r + 1) 2^shift) and holds their
+//     state in shared memory: both record buffers, v and d (FP64), uref, the
+//     list counts and the list columns (cluster_layout).  The device
+//     functions of the graph path run unchanged on a view of Bufs whose
+//     per-atom pointers are redirected there (offset by -r 2^shift);
+//   * neighbour records are read from their owner's buffer through
+//     distributed shared memory;
 //   * the barrier is an mbarrier in every CTA on which each CTA arrives
 //     remotely with release semantics at cluster scope; two alternate, so that
 //     an arrival for the next barrier cannot land in the current phase, and a
@@ -263,10 +269,13 @@ __global__ void __launch_bounds__(256) k_steps(Bufs<R> B, Geom G, Launch L, long
 //   * an arrival can carry the CTA's largest squared displacement, stored
 //     into every CTA's shared memory before the arrive, so that the rebuild
 //     decision reads shared memory instead of a device word;
-//   * optionally (FP32, one fused table) the f and phi rows are copied into
-//     shared memory once per launch.
+//   * a list build writes v and d back, runs the phases of the grid form on
+//     device memory, and loads the new order's state; the launch ends by
+//     writing v, d and the current records back;
+//   * optionally (FP32, one fused table) the f and phi rows sit in shared
+//     memory too.
 // Owned atoms are walked in tiles of blockDim / TPA atoms, so the per-atom
-// work is again that of the graph path, bitwise.
+// arithmetic is that of the graph path, bitwise.
 struct ClusterSync {
     unsigned long long bar[2];
     float dmax[kMaxClusterCtas];  // slot r: CTA r's largest squared displacement
@@ -413,11 +422,12 @@ struct ClusterTab<float, true> {
 
 template <class R, bool MULTI, int TPA, bool TABSM>
 __global__ void __launch_bounds__(kPersistentBlock, 1)
-    k_steps_cluster(Bufs<R> B, Geom G, Launch L, long long nsteps, PersistScratch *ps, int shift)
+    k_steps_cluster(Bufs<R> B, Geom G, Launch L, long long nsteps, PersistScratch *ps, ClusterPlan plan)
 {
     using R4 = typename V4<R>::T;
     constexpr int UD = PairsInFlight<MULTI>::density, UF = PairsInFlight<MULTI>::force;
     __shared__ ClusterSync cs;
+    __shared__ Tables<R> s_tab;
     DevState *st = B.st;
     unsigned *err = &st->error;
     int s = st->set, sp = st->sp, since = st->since_build;
@@ -425,25 +435,57 @@ __global__ void __launch_bounds__(kPersistentBlock, 1)
     int need = 0;
     const int n = L.n, nct = gridDim.x, nthreads = nct * blockDim.x, gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t rank = blockIdx.x;  // the grid is one cluster
-    const int chunk = 1 << shift, a0 = (int)rank << shift, a1 = min(n, a0 + chunk);
+    const int shift = plan.shift;
+    const int chunk = 1 << shift, a0 = (int)rank << shift, a1 = min(n, a0 + chunk), m = a1 - a0;
     const int width = blockDim.x / TPA, l = threadIdx.x % TPA;
-    R4 *const rec0 = reinterpret_cast<R4 *>(dyn);  // record buffers 0 and 1 of the owned atoms
+    const ClusterLayout lay = cluster_layout<R>(chunk, L.cap, plan.nF, TABSM ? L.nint_fused : 0);
+    R4 *const rec0 = reinterpret_cast<R4 *>(dyn + lay.rec);  // buffers 0 and 1 of the owned atoms
+    double *const sv = reinterpret_cast<double *>(dyn + lay.v);
+    double *const sd = reinterpret_cast<double *>(dyn + lay.d);
+    R *const su = reinterpret_cast<R *>(dyn + lay.uref);
+    int *const snnb = reinterpret_cast<int *>(dyn + lay.nnb);
+    uint32_t *const slist = reinterpret_cast<uint32_t *>(dyn + lay.list);
     const float4 *f_rows = nullptr, *phi_rows = nullptr;
     if constexpr (TABSM) {
-        float4 *rows = reinterpret_cast<float4 *>(rec0 + 2 * chunk);
-        const int nint = B.tables->fphi.nint;
-        copy_rows(B.coef2, nint, rows, rows + nint);
+        float4 *rows = reinterpret_cast<float4 *>(dyn + lay.tab);
+        copy_rows(B.coef2, L.nint_fused, rows, rows + L.nint_fused);
         f_rows = rows;
-        phi_rows = rows + nint;
+        phi_rows = rows + L.nint_fused;
     }
     const auto tab = ClusterTab<R, TABSM>::make(B, f_rows, phi_rows);
+    // The view the per-atom device functions run on: owned-atom arrays in
+    // shared memory (indexed by the global atom index), buffer set 0 and
+    // record buffer 0 always the current ones, so that the functions are
+    // called with s = sp = 0 and index nothing dynamically.
+    Bufs<R> V = B;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        V.v[0][c] = V.v[1][c] = sv + c * chunk - a0;
+        V.d[c] = sd + c * chunk - a0;
+        V.uref[c] = su + c * chunk - a0;
+    }
+    V.type[0] = V.type[1] = B.type[s];
+    // the spline descriptors, and the rows of F, in shared memory
+    {
+        const int *src = reinterpret_cast<const int *>(B.tables);
+        int *dst = reinterpret_cast<int *>(&s_tab);
+        for (int w = threadIdx.x; w < (int)(sizeof(Tables<R>) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+        V.tables = &s_tab;
+        if (plan.nF > 0) {
+            R4 *frows = reinterpret_cast<R4 *>(dyn + lay.frows);
+            const int off = B.tables->F[0].offset;
+            for (int q = threadIdx.x; q < plan.nF; q += blockDim.x) frows[q] = B.coef[off + q];
+            V.coef = frows - off;
+        }
+    }
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&cs.bar[0])), "r"(nct) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&cs.bar[1])), "r"(nct) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // every CTA's barriers exist before any remote arrival (all CTAs of a
-    // cluster are resident together and every thread passes here once)
+    // every CTA's barriers exist before any remote arrival, and the copies
+    // above are complete (all CTAs of a cluster are resident together and
+    // every thread passes here once)
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
     unsigned nb = 0;
     auto sync = [&](bool send, float d2) {
@@ -451,16 +493,50 @@ __global__ void __launch_bounds__(kPersistentBlock, 1)
         cluster_leave(ps, nct, err, L.wait_ns);
         return false;
     };
+    // owned state from device memory: v (set s), d, uref, list counts and
+    // columns, and (after a build) the records of buffer sp
+    auto load_owned = [&](bool records) {
+        for (int o = threadIdx.x; o < m; o += blockDim.x) {
+            const int i = a0 + o;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                sv[c * chunk + o] = B.v[s][c][i];
+                sd[c * chunk + o] = B.d[c][i];
+                su[c * chunk + o] = B.uref[c][i];
+            }
+            snnb[o] = B.nnb[i];
+            if (records) rec0[sp * chunk + o] = B.shadow[sp][i];
+        }
+        const int ncol = min(L.cap, st->max_nnb);
+        for (int e = threadIdx.x; e < ncol * m; e += blockDim.x) {
+            const int k = e / m, o = e - k * m;
+            slist[k * chunk + o] = B.list[(size_t)k * L.ld + a0 + o];
+        }
+    };
+    // v and d back to device memory (and the records of buffer sp)
+    auto store_owned = [&](bool records) {
+        for (int o = threadIdx.x; o < m; o += blockDim.x) {
+            const int i = a0 + o;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                B.v[s][c][i] = sv[c * chunk + o];
+                B.d[c][i] = sd[c * chunk + o];
+            }
+            if (records) B.shadow[sp][i] = rec0[sp * chunk + o];
+        }
+    };
+    load_owned(false);
+    __syncthreads();
     R h[3];
     load_h<R>(G, h);
     const R rc2 = g_rc2<R>(G);
 
-    // opening kick and drift from the cached forces
+    // opening kick and drift from the cached forces (record buffer sp ^ 1)
     {
+        V.shadow[0] = rec0 + sp * chunk - a0;
+        V.shadow[1] = rec0 + (sp ^ 1) * chunk - a0;
         float d2 = 0.f;
-        R4 *next = rec0 + (sp ^ 1) * chunk;
-        for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x)
-            d2 = fmaxf(d2, open_atom<R>(B, L, s, sp, i, next + (i - a0)));
+        for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) d2 = fmaxf(d2, open_atom<R>(V, L, 0, 0, i));
         if (!sync(true, d2)) return;
     }
 
@@ -472,9 +548,10 @@ __global__ void __launch_bounds__(kPersistentBlock, 1)
         float md = 0.f;
         for (int r = 0; r < nct; ++r) md = fmaxf(md, cs.dmax[r]);
         need = (since >= L.rebuild_every) || ((double)md > L.disp2_thr);
-        R4 *const cur = rec0 + sp * chunk;
 
         if (need) {
+            store_owned(false);
+            if (!sync(false, 0.f)) return;
             for (int i = gtid; i < n; i += nthreads) bin_atom<R>(B, G, s, i);
             if (!sync(false, 0.f)) return;
             if (rank == 0) scan_cells_block<R>(B, G.ncells);
@@ -483,11 +560,12 @@ __global__ void __launch_bounds__(kPersistentBlock, 1)
             if (!sync(false, 0.f)) return;
             for (int c = gtid; c < G.ncells; c += nthreads) sort_cell<R>(B, s, c);
             if (!sync(false, 0.f)) return;
-            for (int p = a0 + threadIdx.x; p < a1; p += blockDim.x) permute_atom<R>(B, G, s, sp, p, cur + (p - a0));
+            for (int p = gtid; p < n; p += nthreads) permute_atom<R>(B, G, s, sp, p);
             if (gtid == 0) st->max_nnb = 0;
             s = 1 - s;
             since = 0;
             rebuilds += 1;
+            V.type[0] = V.type[1] = B.type[s];
             if (!sync(false, 0.f)) return;
             for (int base = a0; base < a1; base += blockDim.x) {
                 const int p = base + threadIdx.x;
@@ -495,7 +573,13 @@ __global__ void __launch_bounds__(kPersistentBlock, 1)
                 block_max_nnb(cnt, &st->max_nnb);
             }
             if (!sync(false, 0.f)) return;
+            // the other CTAs read these records in the density pass
+            load_owned(true);
+            if (!sync(false, 0.f)) return;
         }
+        R4 *const cur = rec0 + sp * chunk;
+        V.shadow[0] = cur - a0;
+        V.shadow[1] = rec0 + (sp ^ 1) * chunk - a0;
         const ClusterFetch<R> fetch{smem_addr(cur), shift};
 
         // density pass
@@ -504,13 +588,13 @@ __global__ void __launch_bounds__(kPersistentBlock, 1)
             for (int base = a0; base < a1; base += width) {
                 const int i = base + threadIdx.x / TPA;
                 const bool active = i < a1;
-                const int ti = (MULTI && active) ? B.type[s][i] : 0;
+                const int ti = (MULTI && active) ? V.type[0][i] : 0;
                 R rho = (R)0;
                 if (active)
-                    rho = density_lane<R, MULTI, TPA, UD>(B, h, rc2, s, B.nnb + i, L.cap, l, cur[i - a0],
-                                                          ListGlobal{B.list + i, L.ld}, fetch, tab);
+                    rho = density_lane<R, MULTI, TPA, UD>(V, h, rc2, 0, snnb + (i - a0), L.cap, l, cur[i - a0],
+                                                          ListGlobal{slist + (i - a0), chunk}, fetch, tab);
                 rho = lane_sum<TPA>(rho);
-                if (active && l == 0) e_embed += embed<R>(B, B.shadow[sp], i, ti, rho, cur + (i - a0));
+                if (active && l == 0) e_embed += embed<R>(V, V.shadow[0], i, ti, rho);
             }
             if (last) {
                 const R v[1] = {e_embed};
@@ -522,41 +606,30 @@ __global__ void __launch_bounds__(kPersistentBlock, 1)
         // force pass with the closing kick (and, but for the last step, the
         // next opening kick and the drift)
         {
-            R4 *const next = rec0 + (sp ^ 1) * chunk;
             R e7[7] = {0, 0, 0, 0, 0, 0, 0};
             double ke = 0.0;
             float d2max = 0.f;
             for (int base = a0; base < a1; base += width) {
                 const int i = base + threadIdx.x / TPA;
                 const bool active = i < a1;
-                const int ti = (MULTI && active) ? B.type[s][i] : 0;
+                const int ti = (MULTI && active) ? V.type[0][i] : 0;
                 R f[3] = {0, 0, 0};
                 float d2 = 0.f;
-                const ListGlobal list{B.list + i, L.ld};
-                if (active && l == 0) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        prefetch_l1(B.v[s][c] + i);
-                        prefetch_l1(B.d[c] + i);
-                        prefetch_l1(B.uref[c] + i);
-                    }
-                }
+                const ListGlobal list{slist + (i - a0), chunk};
                 if (last) {
                     if (active)
-                        force_lane<R, MULTI, true, TPA, UF>(B, L, h, rc2, s, B.nnb + i, l, ti, cur[i - a0], list,
-                                                            fetch, f, e7, tab);
+                        force_lane<R, MULTI, true, TPA, UF>(V, L, h, rc2, 0, snnb + (i - a0), l, ti, cur[i - a0],
+                                                            list, fetch, f, e7, tab);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);
-                    if (active) integrate<R, MODE_CLOSE, true, TPA>(B, L, s, sp, i, l, ti, f, ke, d2);
+                    if (active) integrate<R, MODE_CLOSE, true, TPA>(V, L, 0, 0, i, l, ti, f, ke, d2);
                 } else {
                     if (active)
-                        force_lane<R, MULTI, false, TPA, UF>(B, L, h, rc2, s, B.nnb + i, l, ti, cur[i - a0], list,
-                                                             fetch, f, e7, tab);
+                        force_lane<R, MULTI, false, TPA, UF>(V, L, h, rc2, 0, snnb + (i - a0), l, ti, cur[i - a0],
+                                                             list, fetch, f, e7, tab);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);
-                    if (active)
-                        integrate<R, MODE_CLOSE_OPEN, false, TPA>(B, L, s, sp, i, l, ti, f, ke, d2,
-                                                                  next + (i - a0));
+                    if (active) integrate<R, MODE_CLOSE_OPEN, false, TPA>(V, L, 0, 0, i, l, ti, f, ke, d2);
                 }
                 d2max = fmaxf(d2max, lane_sum<TPA>(d2));
             }
@@ -571,7 +644,9 @@ __global__ void __launch_bounds__(kPersistentBlock, 1)
         }
     }
 
-    // energies of the last step, counters back to DevState
+    // owned state back to device memory; energies of the last step, counters
+    // back to DevState
+    store_owned(true);
     for (int slot = blockIdx.x; slot < 9; slot += gridDim.x) reduce_slot(B.partials, st, slot, gridDim.x, L.pstride);
     if (gtid == 0) {
         st->set = s;
@@ -653,9 +728,9 @@ cudaError_t launch_steps(const Bufs<R> &B, const Geom &G, const Launch &L, long 
 }
 
 template <class R>
-size_t cluster_smem_bytes(const Launch &L, int shift, bool tabsm)
+size_t cluster_smem_bytes(const Launch &L, int shift, int nF, bool tabsm)
 {
-    return 2 * ((size_t)1 << shift) * sizeof(typename V4<R>::T) + (tabsm ? (size_t)L.nint_fused * 32u : 0u);
+    return cluster_layout<R>(1 << shift, L.cap, nF, tabsm ? L.nint_fused : 0).total;
 }
 
 namespace {
@@ -684,7 +759,7 @@ cudaError_t allow_cluster(const void *fn, size_t smem)
 }  // namespace
 
 template <class R>
-bool cluster_plan(const Launch &L, int tpa, bool tabsm, ClusterPlan &plan)
+bool cluster_plan(const Launch &L, int tpa, bool tabsm, int nF, ClusterPlan &plan)
 {
     if (L.n <= 0 || (tabsm && (!std::is_same<R, float>::value || L.multi || L.nint_fused <= 0))) return false;
     const void *fn = cluster_kernel<R>(L.multi, tabsm, tpa);
@@ -692,10 +767,11 @@ bool cluster_plan(const Launch &L, int tpa, bool tabsm, ClusterPlan &plan)
     while ((1 << shift) < kPersistentBlock / tpa) ++shift;
     for (; shift <= kMaxClusterShift; ++shift) {
         const long long chunk = 1ll << shift;
-        const ClusterPlan p{shift, (int)((L.n + chunk - 1) / chunk)};
+        ClusterPlan p{shift, (int)((L.n + chunk - 1) / chunk), L.multi ? 0 : nF};
         if (p.nct > kMaxClusterCtas) continue;
-        const size_t smem = cluster_smem_bytes<R>(L, shift, tabsm);
-        if (smem > (size_t)kSharedLimitBytes) return false;
+        if (cluster_smem_bytes<R>(L, shift, p.nF, tabsm) > (size_t)kClusterSmemLimit) p.nF = 0;
+        const size_t smem = cluster_smem_bytes<R>(L, shift, p.nF, tabsm);
+        if (smem > (size_t)kClusterSmemLimit) return false;
         if (allow_cluster(fn, smem) != cudaSuccess) {
             cudaGetLastError();
             return false;
@@ -720,7 +796,8 @@ cudaError_t launch_steps_cluster(const Bufs<R> &B, const Geom &G, const Launch &
                                  bool tabsm, const ClusterPlan &plan, PersistScratch *ps)
 {
     const void *fn = cluster_kernel<R>(L.multi, tabsm, tpa);
-    const size_t smem = cluster_smem_bytes<R>(L, plan.shift, tabsm);
+    const size_t smem = cluster_smem_bytes<R>(L, plan.shift, plan.nF, tabsm);
+    if (smem > (size_t)kClusterSmemLimit) return cudaErrorInvalidConfiguration;
     cudaError_t e = allow_cluster(fn, smem);
     if (e == cudaSuccess) e = cudaMemsetAsync(&ps->arrive, 0, sizeof(ps->arrive), L.stream);
     if (e != cudaSuccess) return e;
@@ -731,13 +808,13 @@ cudaError_t launch_steps_cluster(const Bufs<R> &B, const Geom &G, const Launch &
     Launch l = L;
     long long ns = nsteps;
     PersistScratch *p = ps;
-    int sh = plan.shift;
-    void *args[] = {&b, &g, &l, &ns, &p, &sh};
+    ClusterPlan pl = plan;
+    void *args[] = {&b, &g, &l, &ns, &p, &pl};
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-template bool cluster_plan<float>(const Launch &, int, bool, ClusterPlan &);
-template bool cluster_plan<double>(const Launch &, int, bool, ClusterPlan &);
+template bool cluster_plan<float>(const Launch &, int, bool, int, ClusterPlan &);
+template bool cluster_plan<double>(const Launch &, int, bool, int, ClusterPlan &);
 template cudaError_t launch_steps_cluster<float>(const Bufs<float> &, const Geom &, const Launch &, long long, int,
                                                  bool, const ClusterPlan &, PersistScratch *);
 template cudaError_t launch_steps_cluster<double>(const Bufs<double> &, const Geom &, const Launch &, long long, int,

@@ -140,8 +140,7 @@ __device__ __forceinline__ void sort_cell(const Bufs<R> &B, int s, int c)
 // the cell-centred coordinates uref (and record buffer sp) are formed in FP64
 // and rounded.
 template <class R>
-__device__ __forceinline__ void permute_atom(const Bufs<R> &B, const Geom &G, int s, int sp, int p,
-                                             typename V4<R>::T *mirror = nullptr)
+__device__ __forceinline__ void permute_atom(const Bufs<R> &B, const Geom &G, int s, int sp, int p)
 {
     const int t = 1 - s;
     int i = B.cell_atoms[p];
@@ -158,7 +157,6 @@ __device__ __forceinline__ void permute_atom(const Bufs<R> &B, const Geom &G, in
         B.d[a][p] = 0.0;
     }
     B.shadow[sp][p] = mk4<R>(u[0], u[1], u[2], (R)0);
-    if (mirror) *mirror = mk4<R>(u[0], u[1], u[2], (R)0);
     B.id[t][p] = B.id[s][i];
     B.type[t][p] = B.type[s][i];
     B.cell[p] = cell;
@@ -272,8 +270,7 @@ __device__ __forceinline__ void block_max_nnb(int cnt, int *dst)
 // step: v += F dt/(2m), x += v dt; record buffer sp ^ 1 gets the new
 // coordinates.  Returns the squared displacement since the last build (FP32).
 template <class R>
-__device__ __forceinline__ float open_atom(const Bufs<R> &B, const Launch &L, int s, int sp, int i,
-                                           typename V4<R>::T *mirror = nullptr)
+__device__ __forceinline__ float open_atom(const Bufs<R> &B, const Launch &L, int s, int sp, int i)
 {
     int ti = L.ntypes > 1 ? B.type[s][i] : 0;
     double kq = L.half_kick[ti];
@@ -288,7 +285,6 @@ __device__ __forceinline__ float open_atom(const Bufs<R> &B, const Launch &L, in
     }
     R u0 = B.uref[0][i] + (R)dn[0], u1 = B.uref[1][i] + (R)dn[1], u2 = B.uref[2][i] + (R)dn[2];
     B.shadow[sp ^ 1][i] = mk4<R>(u0, u1, u2, (R)0);
-    if (mirror) *mirror = mk4<R>(u0, u1, u2, (R)0);
     float fx = (float)dn[0], fy = (float)dn[1], fz = (float)dn[2];
     return fx * fx + fy * fy + fz * fz;
 }

@@ -210,8 +210,8 @@ def test_cluster_launch_displacement_rebuilds_and_two_types():
 
 def test_cluster_launch_sizes_and_limits():
     """Small and ragged systems: 250 atoms in one CTA, 432 in 7 CTAs of 64
-    (the last holds 48), 1,024 in 16 CTAs of 64 at 4 lanes; above 16 x 2,048
-    atoms md_create refuses the form."""
+    (the last holds 48), 1,024 in 16 CTAs of 64 at 4 lanes; a system whose
+    state does not fit the shared memory of 16 CTAs is refused."""
     for cells, lanes, ncta in ((5, 1, 1), (6, 4, 7), (8, 4, 16)):
         s = I.bcc_cube(cells)
         a, b = run_cluster_pair(s, "mixed", lanes, [15], 2.0)
