@@ -250,6 +250,86 @@ __device__ __forceinline__ int list_atom(const Bufs<R> &B, const Geom &G, int s,
     return cnt;
 }
 
+// list_atom with LT consecutive lanes of a warp on atom p (lane l of the
+// group; LT divides 32): the lanes take slots l, l + LT, ... of each stencil
+// cell, and a ballot over the group places the hits of a round in candidate
+// order, so the list is the one list_atom writes, entry for entry.  The walk
+// per atom is a chain of rounds (about one per cell) instead of one
+// iteration per candidate: the single-launch forms build the lists of a few
+// thousand atoms, where that chain is the whole cost of the build.  Every
+// lane returns the count.
+template <class R, int LT>
+__device__ __forceinline__ int list_atom_lanes(const Bufs<R> &B, const Geom &G, int s, int sp, int p, int ld,
+                                               int cap, int l)
+{
+    static_assert(LT >= 1 && LT <= 32 && (32 % LT) == 0, "lanes per atom must divide 32");
+    using R4 = typename V4<R>::T;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned gmask = LT == 32 ? 0xffffffffu : (((1u << LT) - 1u) << (lane & ~(unsigned)(LT - 1)));
+    const unsigned below = (1u << l) - 1u;
+    int cnt = 0;
+    const double *const xr[3] = {B.xr[s][0], B.xr[s][1], B.xr[s][2]};
+    const R4 *sw = B.shadow[sp];
+    const R lo = g_screen_lo<R>(G), hi = g_screen_hi<R>(G);
+    const R hx = g_h<R>(G, 0), hy = g_h<R>(G, 1), hz = g_h<R>(G, 2);
+    const int nx = G.ncell[0], ny = G.ncell[1], nz = G.ncell[2];
+    const int cell = B.cell[p];
+    const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
+    const R4 up = sw[p];
+    uint32_t *lp = B.list + p;
+    const bool open_x = G.open_mask & 1, open_y = (G.open_mask >> 1) & 1, open_z = (G.open_mask >> 2) & 1;
+#pragma unroll 1
+    for (int dz = -1; dz <= 1; ++dz) {
+        int ez = cz + dz;
+        if (ez < 0 || ez >= nz) {
+            if (open_z) continue;
+            ez += (ez < 0) ? nz : -nz;
+        }
+#pragma unroll 1
+        for (int dy = -1; dy <= 1; ++dy) {
+            int ey = cy + dy;
+            if (ey < 0 || ey >= ny) {
+                if (open_y) continue;
+                ey += (ey < 0) ? ny : -ny;
+            }
+            const int row = (ez * ny + ey) * nx;
+#pragma unroll 1
+            for (int dx = -1; dx <= 1; ++dx) {
+                int ex = cx + dx;
+                if (ex < 0 || ex >= nx) {
+                    if (open_x) continue;
+                    ex += (ex < 0) ? nx : -nx;
+                }
+                const int e = row + ex;
+                const uint32_t code = list_entry(0u, dx, dy, dz);
+                const R ox = (R)dx * hx - up.x, oy = (R)dy * hy - up.y, oz = (R)dz * hz - up.z;
+                const int q0 = B.cell_start[e], q1 = B.cell_start[e + 1];
+                for (int base = q0; base < q1; base += LT) {
+                    const int q = base + l;
+                    bool in = false;
+                    if (q < q1) {
+                        const R4 uq = sw[q];
+                        const R ddx = uq.x + ox, ddy = uq.y + oy, ddz = uq.z + oz;
+                        const R r2 = fma(ddz, ddz, fma(ddy, ddy, ddx * ddx));
+                        in = !(r2 > hi || q == p) && (r2 < lo || exact_in_list(xr, p, q, G));
+                    }
+                    const unsigned hits = (__ballot_sync(gmask, in) & gmask) >> (lane & ~(unsigned)(LT - 1));
+                    if (in) {
+                        const int pos = cnt + __popc(hits & below);
+                        if (pos < cap) lp[(size_t)pos * ld] = (uint32_t)q | code;
+                    }
+                    cnt += __popc(hits & (LT == 32 ? 0xffffffffu : ((1u << LT) - 1u)));
+                }
+            }
+        }
+    }
+    if (l == 0) {
+        B.nnb[p] = min(cnt, cap);
+        if (cnt > cap) atomicOr(&B.st->error, ERR_LIST_OVERFLOW);
+    }
+    return cnt;
+}
+
 // Block maximum of the neighbour counts into st->max_nnb (one atomic per
 // block).  All threads must call.
 __device__ __forceinline__ void block_max_nnb(int cnt, int *dst)
