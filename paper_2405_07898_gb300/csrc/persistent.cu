@@ -91,8 +91,9 @@ __device__ __forceinline__ bool grid_barrier(PersistScratch *ps, unsigned *err, 
     return ok;
 }
 
-// Lanes per atom of the list builds in the single-launch forms (the cluster
-// form has fewer threads for its atoms).
+// Lanes per atom of the list builds in the single-launch forms, taken when
+// one pass of the grid (of the CTA, in the cluster form) covers all its
+// atoms; otherwise one thread walks each atom's stencil.
 constexpr int kListLanes = 8, kListLanesCluster = 4;
 
 // One step loop of nsteps steps (nsteps >= 1).  The counters of DevState
@@ -152,14 +153,19 @@ __global__ void __launch_bounds__(256) k_steps(Bufs<R> B, Geom G, Launch L, long
             since = 0;
             rebuilds += 1;
             if (!grid_barrier(ps, err, L.wait_ns)) return;
-            // kListLanes lanes per atom
-            for (int base = blockIdx.x * (blockDim.x / kListLanes); base < n;
-                 base += gridDim.x * (blockDim.x / kListLanes)) {
-                const int p = base + threadIdx.x / kListLanes;
+            if ((long long)n * kListLanes <= nthreads) {
+                // kListLanes lanes per atom, all atoms in one pass
+                const int p = blockIdx.x * (blockDim.x / kListLanes) + threadIdx.x / kListLanes;
                 const int cnt =
                     (p < n) ? list_atom_lanes<R, kListLanes>(B, G, s, sp, p, L.ld, L.cap, threadIdx.x % kListLanes)
                             : 0;
                 block_max_nnb(cnt, &st->max_nnb);
+            } else {
+                for (int base = blockIdx.x * blockDim.x; base < n; base += nthreads) {
+                    const int p = base + threadIdx.x;
+                    const int cnt = (p < n) ? list_atom<R>(B, G, s, sp, p, L.ld, L.cap) : 0;
+                    block_max_nnb(cnt, &st->max_nnb);
+                }
             }
             if (!grid_barrier(ps, err, L.wait_ns)) return;
         }
@@ -575,12 +581,18 @@ __global__ void __launch_bounds__(kPersistentBlock, 1)
             rebuilds += 1;
             V.type[0] = V.type[1] = B.type[s];
             if (!sync(false, 0.f)) return;
-            for (int base = a0; base < a1; base += blockDim.x / kListLanesCluster) {
-                const int p = base + threadIdx.x / kListLanesCluster;
+            if (m * kListLanesCluster <= (int)blockDim.x) {
+                const int p = a0 + threadIdx.x / kListLanesCluster;
                 const int cnt = (p < a1) ? list_atom_lanes<R, kListLanesCluster>(B, G, s, sp, p, L.ld, L.cap,
                                                                                  threadIdx.x % kListLanesCluster)
                                          : 0;
                 block_max_nnb(cnt, &st->max_nnb);
+            } else {
+                for (int base = a0; base < a1; base += blockDim.x) {
+                    const int p = base + threadIdx.x;
+                    const int cnt = (p < a1) ? list_atom<R>(B, G, s, sp, p, L.ld, L.cap) : 0;
+                    block_max_nnb(cnt, &st->max_nnb);
+                }
             }
             if (!sync(false, 0.f)) return;
             // the other CTAs read these records in the density pass
