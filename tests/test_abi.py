@@ -103,3 +103,35 @@ def test_create_rejects_out_of_range_enums():
                            ctypes.byref(opt), ctypes.byref(h))
         assert rc == -1, (field, rc, lib.md_last_error(None))
         assert not h.value
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every structure the binding passes across the C ABI has the size and
+    field offsets the header gives it (a small C program compiled with gcc
+    prints them)."""
+    pairs = [(binding.Spline, "md_spline"), (binding.PotentialC, "md_potential"),
+             (binding.Options, "md_options"), (binding.Stats, "md_stats_t"),
+             (binding.Profile, "md_profile_t"), (binding.Replica, "md_replica"),
+             (binding.BatchInfo, "md_batch_info_t")]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "eammd.h"', "int main(void) {"]
+    for cls, cname in pairs:
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            cname, key, val = line.split()
+            got[(cname, key)] = int(val)
+    for cls, cname in pairs:
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for field, _ in cls._fields_:
+            assert got[(cname, field)] == getattr(cls, field).offset, (cname, field)
