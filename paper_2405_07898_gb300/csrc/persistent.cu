@@ -1,9 +1,10 @@
-// persistent.cu -- md_step as one cooperative launch: every phase of every
-// step (opening kick, rebuild decision, list rebuild, density, force with the
-// kicks and the drift, energy sums) runs in one kernel whose blocks meet at
-// grid barriers.  For small systems, where a step is a few microseconds of
-// work, this removes the per-kernel launch and scheduling gaps of the graph
-// path.  The per-atom arithmetic is that of the graph path (same device
+// persistent.cu -- md_step as one launch: every phase of every step (opening
+// kick, rebuild decision, list rebuild, density, force with the kicks and the
+// drift, energy sums) runs in one kernel, either a cooperative grid whose
+// blocks meet at grid barriers (k_steps) or one thread-block cluster
+// (k_steps_cluster, below).  For small systems, where a step is a few
+// microseconds of work, this removes the per-kernel launch and scheduling
+// gaps of the graph path.  The per-atom arithmetic is that of the graph path (same device
 // functions, same lanes per atom), so positions, velocities and forces are
 // bitwise equal; energy sums differ in rounding only (other block partition).
 //
@@ -267,8 +268,10 @@ __global__ void __launch_bounds__(256) k_steps(Bufs<R> B, Geom G, Launch L, long
 // (arrival and release) whose release also waits for the block's stores to
 // reach L2, and after its acquire every list column, count and neighbour
 // record comes from L2 again.  Here the step loop runs in one cluster of at
-// most 16 CTAs and, between list builds, touches device memory only for the
-// embedding-function rows:
+// most 16 CTAs and, between list builds, reads device memory only for what
+// does not fit or is type-dependent (the f and phi rows unless they are
+// copied, the neighbour types and spline rows of several types) and writes it
+// only for the cached forces of the last step:
 //   * CTA r owns the atoms [r 2^shift, (r + 1) 2^shift) and holds their
 //     state in shared memory: both record buffers, v and d (FP64), uref, the
 //     list counts and the list columns (cluster_layout).  The device
@@ -286,8 +289,9 @@ __global__ void __launch_bounds__(256) k_steps(Bufs<R> B, Geom G, Launch L, long
 //   * a list build writes v and d back, runs the phases of the grid form on
 //     device memory, and loads the new order's state; the launch ends by
 //     writing v, d and the current records back;
-//   * optionally (FP32, one fused table) the f and phi rows sit in shared
-//     memory too.
+//   * the spline descriptors and, where they fit, the rows of F sit in
+//     shared memory, and optionally (FP32, one fused table) the f and phi
+//     rows too.
 // Owned atoms are walked in tiles of blockDim / TPA atoms, so the per-atom
 // arithmetic is that of the graph path, bitwise.
 struct ClusterSync {
