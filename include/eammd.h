@@ -330,13 +330,20 @@ md_status md_force_match(md_ctx *ctx, const double *f_ref, double e_ref, double 
  * uses ncell_d = floor(box_d / r_list) cells per axis (each >= 3), and writes
  * d_cell_start[ncells+1] and d_cell_atoms[n] (atom indices, ascending inside
  * each cell; both device memory, caller-owned), queued on cuda_stream (NULL =
- * the legacy default stream); it does not synchronise.
- * Scratch lives in one static device array of about 2.4 MB that every GPU
+ * the legacy default stream); it does not synchronise.  The order inside a
+ * cell comes from sorting the distinct keys (cell, index), so its cost is
+ * O(n log^2 n) however the atoms crowd into cells.  A non-finite coordinate
+ * cannot be detected here (the call does not synchronise): such an atom is
+ * binned into cell 0 along that axis, whereas md_create and md_set_state
+ * reject non-finite positions with MD_ERR_NONFINITE, so for such input there
+ * is no md_cells result to equal.
+ * Scratch lives in one static device array of about 2.3 MB that every GPU
  * loading this library holds until the process exits.  Limits: n <= 262,144
  * atoms and ncells <= 65,536; larger inputs return MD_ERR_CAPACITY, and no
  * work is queued.  Other errors: MD_ERR_ARG, MD_ERR_BOX (an axis with fewer
- * than 3 cells), MD_ERR_CUDA; this entry point has no context, so
- * md_last_error() does not describe its failures.
+ * than 3 cells), MD_ERR_CUDA (a launch of this call failed; each launch's
+ * own status is checked and no earlier error is consumed); this entry point
+ * has no context, so md_last_error() does not describe its failures.
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
  * before any stream capture.  Every call shares the one array: calls that

@@ -729,11 +729,18 @@ int orc_force_match(const orc_pot *p, int64_t n, const double box[3], int open, 
     double *drho = calloc(nn, sizeof(double));
     int64_t cap = 64 * (int64_t)nn;
     int32_t *js = malloc(sizeof(int32_t) * (size_t)cap);
-    if (!wp || !types || !off || !rho || !Fp || !force || !g || !drho || !js) return -2;
+    int status = 0;
+    if (!wp || !types || !off || !rho || !Fp || !force || !g || !drho || !js) {
+        status = -2;
+        goto done;
+    }
     memcpy(wp, pos, sizeof(double) * 3 * (size_t)n);
     orc_wrap(n, box, open, wp);
     int64_t m = orc_list_cells(n, box, open, p->r_cut + p->skin, wp, off, js, cap);
-    if (m < 0 || m > cap) return -3;
+    if (m < 0 || m > cap) {
+        status = -3;
+        goto done;
+    }
     double energy[2], vir[6];
     orc_eam_eval(p, n, box, open, wp, types, off, js, rho, Fp, force, energy, vir);
     double E = energy[0] + energy[1];
@@ -787,6 +794,7 @@ int orc_force_match(const orc_pot *p, int64_t n, const double box[3], int open, 
     }
     if (e_out) *e_out = E;
     if (f_out) memcpy(f_out, force, sizeof(double) * 3 * (size_t)n);
+done:
     free(wp); free(types); free(off); free(rho); free(Fp); free(force); free(g); free(drho); free(js);
-    return 0;
+    return status;
 }

@@ -1,17 +1,25 @@
 // noalloc_bins.cu -- a cell binner that allocates no device memory.
 //
 // md_bin_cells_noalloc() sorts atoms into cells like the binning stage of the
-// list rebuild (counting sort, ascending atom index inside a cell), but
-// reads the caller's device positions, writes the caller's device outputs,
-// and keeps its scratch (cell of each atom, rank inside its cell, per-cell
+// list rebuild (cells in x-fastest order, ascending atom index inside a
+// cell), but reads the caller's device positions, writes the caller's device
+// outputs, and keeps its scratch (one 64-bit sort key per atom, per-cell
 // counts, per-block sums) in the file-scope device array below instead of
 // memory from cudaMalloc.  Every GPU that loads the library holds that array
 // until the process exits.
+//
+// Order inside a cell: each atom's key is (cell << 32) | index, and the keys
+// are put in order by a bitonic sorting network.  The keys are distinct, so
+// the result is the one stable order whatever the input; the work is
+// O(N log^2 N) for N = the next power of two >= n (at least 2,048), however
+// the atoms are spread over the cells.  The per-cell counts come from integer
+// atomics, whose totals do not depend on arrival order.
 #include "eammd.h"
 
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 
 namespace {
@@ -20,15 +28,17 @@ constexpr int kNoAllocMaxAtoms = 1 << 18;  // 262,144 atoms
 constexpr int kNoAllocMaxCells = 1 << 16;  // 65,536 cells
 constexpr int kNbScanBlock = 1024;
 constexpr int kNbMaxScanBlocks = kNoAllocMaxCells / kNbScanBlock;
-// layout (ints): cell of atom [0, A), rank in cell [A, 2A), count [2A, 2A+C),
-// block sums [2A+C, 2A+C+B)
-constexpr size_t kScratchInts = 2 * (size_t)kNoAllocMaxAtoms + kNoAllocMaxCells + kNbMaxScanBlocks;
+constexpr int kSortChunk = 2048;  // keys one block orders in shared memory
+// layout (8-byte words): sort keys [0, A); then (ints) count [0, C) and
+// block sums [C, C + B)
+constexpr size_t kScratchWords =
+    (size_t)kNoAllocMaxAtoms + ((size_t)kNoAllocMaxCells + kNbMaxScanBlocks + 1) / 2;
 
-static __device__ __align__(256) int g_bin_scratch[kScratchInts];
+static __device__ __align__(256) unsigned long long g_bin_scratch[kScratchWords];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-int *g_scratch_addr[kMaxDevices] = {nullptr};
+unsigned long long *g_scratch_addr[kMaxDevices] = {nullptr};
 
 struct BinGeom {
     double box[3];
@@ -44,11 +54,17 @@ __global__ void k_nb_clear(int *count, int ncells)
 }
 
 // periodic image (x kept in [0, L), else x - L floor(x/L)), then
-// c_d = min(floor(x_d n_d / L_d), n_d - 1)
-__global__ void k_nb_bin(const double *pos, int n, BinGeom G, int *cell_of, int *rank, int *count)
+// c_d = min(floor(x_d n_d / L_d), n_d - 1); a non-finite coordinate gives
+// cell 0 on its axis.  Keys at and beyond n (up to nsort) are padding that
+// orders after every real key.
+__global__ void k_nb_bin(const double *pos, int n, int nsort, BinGeom G, unsigned long long *keys, int *count)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= nsort) return;
+    if (i >= n) {
+        keys[i] = ~0ull;
+        return;
+    }
     int c[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -62,8 +78,8 @@ __global__ void k_nb_bin(const double *pos, int n, BinGeom G, int *cell_of, int 
         c[a] = isfinite(y) ? (int)fmax(fmin(y, (double)(G.ncell[a] - 1)), 0.0) : 0;
     }
     int cell = (c[2] * G.ncell[1] + c[1]) * G.ncell[0] + c[0];
-    cell_of[i] = cell;
-    rank[i] = atomicAdd(&count[cell], 1);
+    keys[i] = ((unsigned long long)(unsigned)cell << 32) | (unsigned)i;
+    atomicAdd(&count[cell], 1);
 }
 
 __global__ void k_nb_block_sums(const int *count, int ncells, int *block_sums)
@@ -119,33 +135,78 @@ __global__ void k_nb_scan(const int *count, const int *block_sums, int ncells, i
     }
 }
 
-__global__ void k_nb_scatter(const int *cell_of, const int *rank, const int *cell_start, int n, int *cell_atoms)
+// One compare-exchange of the bitonic network: stage k (the length of the
+// sequences being merged), distance j.  Element i pairs with i ^ j; the pair
+// is put in ascending order when bit k of i is clear, else descending.
+__device__ __forceinline__ void bitonic_cx(unsigned long long *a, unsigned i, unsigned j, unsigned k)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    cell_atoms[cell_start[cell_of[i]] + rank[i]] = i;
+    const unsigned l = i ^ j;
+    if (l <= i) return;
+    const unsigned long long x = a[i], y = a[l];
+    if ((x > y) == ((i & k) == 0)) {
+        a[i] = y;
+        a[l] = x;
+    }
 }
 
-// ascending atom index inside each cell (atomics leave arrival order)
-__global__ void k_nb_sort(const int *cell_start, int ncells, int *cell_atoms)
+// All steps of distance j < kSortChunk for the stages k in [k_lo, k_hi] on
+// one 2,048-key chunk in shared memory (blockDim.x == kSortChunk / 2).  For
+// k_lo = 2 this orders each chunk from scratch; for one k > kSortChunk it
+// finishes that stage after the global steps of larger distances.
+__global__ void k_nb_sort_chunk(unsigned long long *keys, unsigned k_lo, unsigned k_hi)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncells) return;
-    int s = cell_start[c], e = cell_start[c + 1];
-    for (int q = s + 1; q < e; ++q) {
-        int a = cell_atoms[q];
-        int r = q - 1;
-        while (r >= s && cell_atoms[r] > a) {
-            cell_atoms[r + 1] = cell_atoms[r];
-            --r;
+    __shared__ unsigned long long sm[kSortChunk];
+    const unsigned base = blockIdx.x * kSortChunk;
+    for (unsigned t = threadIdx.x; t < (unsigned)kSortChunk; t += blockDim.x) sm[t] = keys[base + t];
+    __syncthreads();
+    for (unsigned k = k_lo; k <= k_hi; k <<= 1) {
+        for (unsigned j = min(k >> 1, (unsigned)kSortChunk >> 1); j > 0; j >>= 1) {
+            // thread t handles the pair whose lower index is the t-th index
+            // with bit j clear
+            const unsigned t = threadIdx.x;
+            const unsigned i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+            const unsigned l = i | j;
+            const unsigned long long x = sm[i], y = sm[l];
+            const bool up = ((base + i) & k) == 0;
+            if ((x > y) == up) {
+                sm[i] = y;
+                sm[l] = x;
+            }
+            __syncthreads();
         }
-        cell_atoms[r + 1] = a;
     }
+    for (unsigned t = threadIdx.x; t < (unsigned)kSortChunk; t += blockDim.x) keys[base + t] = sm[t];
+}
+
+// One step of distance j >= kSortChunk of stage k over all nsort keys.
+__global__ void k_nb_sort_step(unsigned long long *keys, unsigned nsort, unsigned j, unsigned k)
+{
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nsort) bitonic_cx(keys, i, j, k);
+}
+
+__global__ void k_nb_extract(const unsigned long long *keys, int n, int *cell_atoms)
+{
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) cell_atoms[q] = (int)(unsigned)(keys[q] & 0xffffffffull);
+}
+
+// Each launch reports its own status, and no earlier error of the caller's
+// is consumed.
+template <class... KArgs, class... Args>
+cudaError_t launch(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 // Device address of the scratch array for the current device, looked up once
 // per device (the first call on a device does it, with that device current).
-md_status scratch_for_current_device(int **out)
+md_status scratch_for_current_device(unsigned long long **out)
 {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -156,7 +217,7 @@ md_status scratch_for_current_device(int **out)
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_bin_scratch);
         if (e != cudaSuccess || !p) return MD_ERR_CUDA;
-        g_scratch_addr[dev] = static_cast<int *>(p);
+        g_scratch_addr[dev] = static_cast<unsigned long long *>(p);
     }
     *out = g_scratch_addr[dev];
     return MD_OK;
@@ -184,23 +245,35 @@ extern "C" md_status md_bin_cells_noalloc(const double box[3], double r_list, in
     if (ncells > kNoAllocMaxCells) return MD_ERR_CAPACITY;   // more than 65,536 cells
     if ((n > 0 && (!d_pos || !d_cell_atoms)) || !d_cell_start) return MD_ERR_ARG;
     G.ncells = (int)ncells;
-    int *scratch = nullptr;
+    unsigned long long *scratch = nullptr;
     md_status rc = scratch_for_current_device(&scratch);
     if (rc != MD_OK) return rc;
-    int *cell_of = scratch;
-    int *rank = scratch + kNoAllocMaxAtoms;
-    int *count = scratch + 2 * (size_t)kNoAllocMaxAtoms;
+    unsigned long long *keys = scratch;
+    int *count = reinterpret_cast<int *>(scratch + kNoAllocMaxAtoms);
     int *block_sums = count + kNoAllocMaxCells;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    const int nb = (int)((n + 255) / 256), ncb = (G.ncells + 255) / 256;
+    const int ncb = (G.ncells + 255) / 256;
     const int nsb = (G.ncells + kNbScanBlock - 1) / kNbScanBlock;
-    k_nb_clear<<<ncb, 256, 0, s>>>(count, G.ncells);
-    if (n > 0) k_nb_bin<<<nb, 256, 0, s>>>(d_pos, (int)n, G, cell_of, rank, count);
-    k_nb_block_sums<<<nsb, 256, 0, s>>>(count, G.ncells, block_sums);
-    k_nb_scan<<<nsb, kNbScanBlock, 0, s>>>(count, block_sums, G.ncells, d_cell_start);
+    unsigned nsort = kSortChunk;
+    while (nsort < (unsigned)n) nsort <<= 1;  // <= kNoAllocMaxAtoms
+    cudaError_t e = launch(k_nb_clear, ncb, 256, s, count, G.ncells);
+    if (e == cudaSuccess && n > 0)
+        e = launch(k_nb_bin, (nsort + 255) / 256, 256, s, d_pos, (int)n, (int)nsort, G, keys, count);
+    if (e == cudaSuccess) e = launch(k_nb_block_sums, nsb, 256, s, (const int *)count, G.ncells, block_sums);
+    if (e == cudaSuccess)
+        e = launch(k_nb_scan, nsb, kNbScanBlock, s, (const int *)count, (const int *)block_sums, G.ncells,
+                   (int *)d_cell_start);
     if (n > 0) {
-        k_nb_scatter<<<nb, 256, 0, s>>>(cell_of, rank, d_cell_start, (int)n, d_cell_atoms);
-        k_nb_sort<<<ncb, 256, 0, s>>>(d_cell_start, G.ncells, d_cell_atoms);
+        const unsigned chunks = nsort / kSortChunk;
+        if (e == cudaSuccess) e = launch(k_nb_sort_chunk, chunks, kSortChunk / 2, s, keys, 2u, (unsigned)kSortChunk);
+        for (unsigned k = 2 * kSortChunk; k <= nsort && e == cudaSuccess; k <<= 1) {
+            for (unsigned j = k >> 1; j >= (unsigned)kSortChunk && e == cudaSuccess; j >>= 1)
+                e = launch(k_nb_sort_step, nsort / 256, 256, s, keys, nsort, j, k);
+            if (e == cudaSuccess) e = launch(k_nb_sort_chunk, chunks, kSortChunk / 2, s, keys, k, k);
+        }
+        if (e == cudaSuccess)
+            e = launch(k_nb_extract, (unsigned)((n + 255) / 256), 256, s, (const unsigned long long *)keys, (int)n,
+                       (int *)d_cell_atoms);
     }
-    return cudaGetLastError() == cudaSuccess ? MD_OK : MD_ERR_CUDA;
+    return e == cudaSuccess ? MD_OK : MD_ERR_CUDA;
 }

@@ -6,6 +6,7 @@ import pytest
 
 import oracle as O
 from paper_2405_07898_gb300 import autodiff, binding, inputs as I
+from bars import assert_forces
 
 pytestmark = pytest.mark.gpu
 
@@ -34,7 +35,7 @@ def test_references_match_oracle(small):
     for (pos, box), (e, f) in zip(prob.configs, fm.refs):
         _, _, F, E, _ = O.eam_eval(ref, O.wrap(pos, box), box, np.zeros(len(pos), np.int32))
         assert abs(e - E.sum()) / abs(E.sum()) < 1e-10
-        assert rel(f, F) < 1e-10
+        assert_forces(f, F, "fp64")
 
 
 def test_gradient_matches_oracle_adjoint(small):
@@ -114,7 +115,7 @@ def test_set_potential_keeps_grids():
         p2.phi[0].y = p2.phi[0].y * 1.1
         md.set_potential(p2)
         _, _, F, _, _ = O.eam_eval(O.Potential(p2), O.wrap(s.pos, s.box), s.box, s.types)
-        assert rel(md.forces(), F) < 1e-10
+        assert_forces(md.forces(), F, "fp64")
 
 
 def test_worker_threads_give_the_same_loss_and_gradient():

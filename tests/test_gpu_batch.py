@@ -6,6 +6,7 @@ import pytest
 
 import oracle as O
 from paper_2405_07898_gb300 import binding, inputs as I
+from bars import assert_forces
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +42,7 @@ def test_initial_forces_and_energies_per_replica():
         for r, s in enumerate(systems):
             _, _, F, E, _ = oracle_state(s)
             _, _, f = b.get_state(r)
-            assert rel(f, F) < MIXED_TOL, r
+            assert_forces(f, F, "mixed", f"replica {r}")
             assert abs(pe[r] - E.sum()) / abs(E.sum()) < MIXED_TOL
             m = s.pot.mass[0]
             ke_ref = 0.5 * m * (s.vel**2).sum() / I.ACCEL_EV_A_AMU
@@ -67,7 +68,7 @@ def test_trajectories_against_oracle():
             assert abs((pe[r] + ke[r]) - (ope + oke)) / abs(ope + oke) < 1e-5, r
             # forces at the batch's own positions
             _, _, F, _, _ = oracle_state(s, pos)
-            assert rel(f, F) < MIXED_TOL, r
+            assert_forces(f, F, "mixed", f"replica {r}")
 
 
 def test_batch_equals_itself_and_graphs_equal_plain_launches():
@@ -107,9 +108,43 @@ def test_every_block_shape_gives_the_same_trajectories():
     for sched in range(1, 6):
         with binding.MDBatch(systems, schedule=sched) as b:
             for r in range(len(systems)):
-                assert rel(b.get_state(r)[2], refs[r]) < MIXED_TOL, (sched, r)
+                assert_forces(b.get_state(r)[2], refs[r], "mixed", f"schedule {sched} replica {r}")
             b.step(20, 2.0)
             out.append([b.get_state(r)[0] for r in range(len(systems))])
     for o in out[1:]:
         for a, c in zip(o, out[0]):
             np.testing.assert_array_equal(a, c)
+
+
+def test_full_512_replica_batch_sample_against_oracle():
+    """The batched workload the benchmark times: 512 replicas (about 3.0 M
+    atoms; BCC and FCC; 1,024 to 16,384 atoms; 200 to 1,200 K) in one launch
+    with its largest-first queue and the timed block shape.  A seeded sample
+    of 16 replicas, always including the largest BCC and the largest FCC
+    replica, is checked against the oracle at step 0 and after 100 steps:
+    every atom's force at the batch's own positions (both bars), the
+    potential energy, and the kinetic energy from the batch's velocities."""
+    systems = I.replica_batch()
+    n = np.array([s.n for s in systems])
+    half = len(systems) // 2
+    big_bcc = int(np.argmax(n[:half]))
+    big_fcc = half + int(np.argmax(n[half:]))
+    rng = np.random.Generator(np.random.PCG64(I.SEED_BASE + 512))
+    rest = [r for r in range(len(systems)) if r not in (big_bcc, big_fcc)]
+    sample = [big_bcc, big_fcc] + sorted(int(r) for r in rng.choice(rest, 14, replace=False))
+    assert n[big_bcc] > 14000 and n[big_fcc] > 14000
+    with binding.MDBatch(systems) as b:
+        for r in sample:
+            _, _, F, _, _ = oracle_state(systems[r])
+            assert_forces(b.get_state(r)[2], F, "mixed", f"step 0 replica {r}")
+        b.step(100, 2.0)
+        pe, ke = b.energy()
+        for r in sample:
+            s = systems[r]
+            pos, vel, f = b.get_state(r)
+            _, _, F, E, _ = oracle_state(s, pos)
+            assert_forces(f, F, "mixed", f"step 100 replica {r} ({s.n} atoms)")
+            assert abs(pe[r] - E.sum()) / abs(E.sum()) < MIXED_TOL, r
+            m = s.pot.mass[0]
+            ke_ref = 0.5 * m * (vel**2).sum() / I.ACCEL_EV_A_AMU
+            assert abs(ke[r] - ke_ref) / ke_ref < 1e-9, r

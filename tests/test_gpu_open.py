@@ -12,6 +12,7 @@ import pytest
 
 import oracle as O
 from paper_2405_07898_gb300 import binding, inputs as I
+from bars import assert_forces
 
 pytestmark = pytest.mark.gpu
 
@@ -69,7 +70,7 @@ def test_open_forces_energy_virial(open_axes, precision):
     s = I.bcc_slab_small(open_axes)
     _, _, F, E, W = oracle_eval(s)
     with binding.MD(s, precision=precision) as md:
-        assert rel(md.forces(), F) < TOL[precision]
+        assert_forces(md.forces(), F, precision)
         pe, _ = md.energy()
         assert abs(pe - E.sum()) / abs(E.sum()) < TOL[precision]
         assert rel(md.virial(), W) < TOL[precision]
@@ -89,7 +90,7 @@ def test_open_trajectory_fp64_matches_oracle():
             assert np.abs(vel - st["vel"]).max() < 1e-11
         assert md.stats()["rebuilds"] == ref.state()["rebuilds"] == 10
         _, _, F, _, _ = oracle_eval(s, pos)
-        assert rel(md.forces(), F) < TOL["fp64"]
+        assert_forces(md.forces(), F, "fp64")
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -112,7 +113,7 @@ def test_open_schedules_and_single_launch_bitwise(precision):
         for a, b in zip(out[name], out["atoms"]):
             np.testing.assert_array_equal(a, b)
     _, _, F, _, _ = oracle_eval(s, out["atoms"][1])
-    assert rel(out["atoms"][2], F) < TOL[precision]
+    assert_forces(out["atoms"][2], F, precision)
 
 
 def test_paper_size_ta_slab_forces():
@@ -121,14 +122,14 @@ def test_paper_size_ta_slab_forces():
     s = I.ta_slab_801792()
     _, _, F, E, _ = oracle_eval(s)
     with binding.MD(s, precision="mixed") as md:
-        assert rel(md.forces(), F) < TOL["mixed"]
+        assert_forces(md.forces(), F, "mixed")
         pe, _ = md.energy()
         assert abs(pe - E.sum()) / abs(E.sum()) < TOL["mixed"]
         md.step(10, 2.0)
         pos, _, _ = md.get_state()
         f10 = md.forces()
     _, _, F10, _, _ = oracle_eval(s, pos)
-    assert rel(f10, F10) < TOL["mixed"]
+    assert_forces(f10, F10, "mixed")
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -139,6 +140,6 @@ def test_open_fcc_slab_forces(precision):
     _, _, F, E, _ = oracle_eval(s)
     with binding.MD(s, precision=precision) as md:
         assert md.stats()["max_neighbors"] >= 54
-        assert rel(md.forces(), F) < TOL[precision]
+        assert_forces(md.forces(), F, precision)
         pe, _ = md.energy()
         assert abs(pe - E.sum()) / abs(E.sum()) < TOL[precision]

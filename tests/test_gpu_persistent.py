@@ -12,6 +12,7 @@ import pytest
 
 import oracle as O
 from paper_2405_07898_gb300 import binding, inputs as I
+from bars import assert_forces
 
 pytestmark = pytest.mark.gpu
 
@@ -58,7 +59,7 @@ def test_single_launch_equals_graphs(precision, lanes):
     for x, y in zip(a["energy"], b["energy"]):
         assert abs(x - y) <= ETOL[precision] * abs(y)
     np.testing.assert_allclose(a["virial"], b["virial"], rtol=ETOL[precision] * 100, atol=1e-12)
-    assert rel(a["forces"], oracle_forces(s, a["pos"])) < TOL[precision]
+    assert_forces(a["forces"], oracle_forces(s, a["pos"]), precision)
 
 
 def test_single_launch_displacement_rebuilds():
@@ -95,7 +96,7 @@ def test_single_launch_two_types_and_uneven_cells():
                    types=np.zeros(len(pos), np.int32), pot=I.johnson_potential(I.BCC_TA_LIKE))
     a, b = run_pair(gas, "fp64", 1, [30], 1.0)
     np.testing.assert_array_equal(a["pos"], b["pos"])
-    assert rel(a["forces"], oracle_forces(gas, a["pos"])) < TOL["fp64"]
+    assert_forces(a["forces"], oracle_forces(gas, a["pos"]), "fp64")
 
 
 def test_single_launch_after_set_state_and_auto_threshold():
@@ -133,7 +134,7 @@ def test_wait_limit_raises_timeout_and_the_context_recovers(form):
             md.sync()
         assert e.value.status == -6  # MD_ERR_TIMEOUT
         md.set_state(s.pos, s.vel, 0)
-        assert rel(md.forces(), oracle_forces(s, s.pos)) < TOL["mixed"]
+        assert_forces(md.forces(), oracle_forces(s, s.pos), "mixed")
     with pytest.raises(binding.MDError) as e:
         binding.MD(s, wait_limit_us=-1)
     assert e.value.status == -1
@@ -182,7 +183,7 @@ def test_cluster_launch_equals_graphs(precision, lanes):
     # rounding relative to the tensor's scale (off-diagonals are cancellations)
     np.testing.assert_allclose(a["virial"], b["virial"], rtol=0,
                                atol=ETOL[precision] * 100 * np.abs(b["virial"]).max())
-    assert rel(a["forces"], oracle_forces(s, a["pos"])) < TOL[precision]
+    assert_forces(a["forces"], oracle_forces(s, a["pos"]), precision)
 
 
 @pytest.mark.parametrize("lanes", [1, 4])

@@ -14,6 +14,7 @@ import pytest
 
 import oracle as O
 from paper_2405_07898_gb300 import binding, inputs as I
+from bars import assert_forces
 
 pytestmark = pytest.mark.gpu
 
@@ -82,7 +83,7 @@ def test_schedule_equals_atoms_and_oracle(c1, schedule, precision, lanes):
         for k in FLAGS:
             assert sb[k] == 0
         np.testing.assert_array_equal(a.forces(), b.forces())
-        assert rel(a.forces(), F) < TOL[precision]
+        assert_forces(a.forces(), F, precision)
         pe, _ = a.energy()
         assert abs(pe - E.sum()) / abs(E.sum()) < TOL[precision]
         assert rel(a.virial(), W) < TOL[precision]
@@ -101,7 +102,7 @@ def test_schedule_equals_atoms_and_oracle(c1, schedule, precision, lanes):
     _, _, F2, _, _ = oracle_eval(c1, pa)
     with binding.MD(c1, schedule=schedule, **kw) as c:
         c.set_state(pa, va, 37)
-        assert rel(c.forces(), F2) < TOL[precision]
+        assert_forces(c.forces(), F2, precision)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -120,7 +121,7 @@ def test_rows_with_blocks_past_the_stage(precision):
             assert a.stats()["stage_capacity"] == cap
             _, _, F, _, _ = oracle_eval(s)
             np.testing.assert_array_equal(a.forces(), b.forces())
-            assert rel(a.forces(), F) < TOL[precision]
+            assert_forces(a.forces(), F, precision)
             a.step(40, 1.0)
             b.step(40, 1.0)
             pa, _, _ = a.get_state()
@@ -128,7 +129,7 @@ def test_rows_with_blocks_past_the_stage(precision):
             np.testing.assert_array_equal(pa, pb)
             np.testing.assert_array_equal(a.forces(), b.forces())
             _, _, F2, _, _ = oracle_eval(s, pa)
-            assert rel(a.forces(), F2) < TOL[precision]
+            assert_forces(a.forces(), F2, precision)
 
 
 @pytest.mark.parametrize("schedule", ["tiles", "table"])
@@ -167,7 +168,7 @@ def test_rows_rejections_and_multi_type_fallback():
                 st = md.stats()
                 for k in FLAGS:
                     assert st[k] == 0
-                assert rel(md.forces(), F) < TOL[precision]
+                assert_forces(md.forces(), F, precision)
 
 
 def test_autotuned_schedule_is_deterministic():
