@@ -249,9 +249,6 @@ def run_ours(args):
             "clocks": clk,
             "stats": {"rebuilds": st["rebuilds"], "max_neighbors": st["max_neighbors"],
                       "lanes_density": st["lanes_density"], "lanes_force": st["lanes_force"],
-                      "rows_density": st["rows_density"], "rows_force": st["rows_force"],
-                      "tiles_density": st["tiles_density"], "tiles_force": st["tiles_force"],
-                      "table_density": st["table_density"], "table_force": st["table_force"],
                       "threads_density": st["threads_density"], "threads_force": st["threads_force"]},
         }
         if cpu is not None:
@@ -277,10 +274,9 @@ def _timed_steps(md, nsteps, dt, reps=1):
 def run_sweep(args):
     """Strong-scaling sweep: BCC cubes of 1,024 .. 314,928 atoms and the
     799,496-atom box at 1,000 K (mixed precision): timesteps/s of md_step
-    replayed as CUDA graphs, up to 314,928 atoms as one cooperative launch per
-    call, and, where the system fits the shared memory of 16 CTAs, as one
-    thread-block cluster per call (the library times the single-launch forms
-    and takes one automatically up to 65,536 atoms)."""
+    replayed as CUDA graphs, and up to 314,928 atoms as one cooperative launch
+    per call (the library takes the single launch automatically up to 65,536
+    atoms)."""
     import torch
     from paper_2405_07898_gb300 import binding, inputs as I
 
@@ -289,26 +285,19 @@ def run_sweep(args):
     for s in I.sweep_systems(temperature=1000.0):
         steps = max(200, min(20000, int(2e8 // s.n) // 10 * 10))
         row = {"atoms": s.n, "steps": steps}
-        for mode in ("off", "on", "cluster"):
-            if (mode == "on" and s.n > 400000) or (mode == "cluster" and s.n > 16384):
+        for mode in ("off", "on"):
+            if mode == "on" and s.n > 400000:
                 continue
-            try:
-                md = binding.MD(s, precision="mixed", persistent=mode)
-            except binding.MDError:
-                if mode == "cluster":  # the system does not fit one cluster
-                    continue
-                raise
+            md = binding.MD(s, precision="mixed", persistent=mode)
             md.step(100, DT_FS)
             t = _timed_steps(md, steps, DT_FS)
-            key = {"off": "graph", "on": "single_launch", "cluster": "cluster"}[mode]
+            key = {"off": "graph", "on": "single_launch"}[mode]
             row[key + "_ts_per_s"] = steps / t
             row[key + "_atom_steps_per_s"] = s.n * steps / t
             if mode != "off":
                 st = md.stats()
                 row[key + "_blocks"] = st["persistent_blocks"]
                 row[key + "_lanes"] = st["persistent_lanes"]
-                if mode == "cluster":
-                    row["cluster_shared_tables"] = int(st["persistent_cluster"] == 2)
             md.close()
         rows.append(row)
     print(json.dumps({"workload": "bcc_sweep_1000K_mixed", "unit": "timesteps/s", "sweep": rows}), flush=True)

@@ -82,9 +82,7 @@ typedef struct {
 } md_potential;
 
 enum { MD_PRECISION_FP64 = 0, MD_PRECISION_MIXED = 1 };
-enum { MD_PERSIST_AUTO = 0, MD_PERSIST_OFF = 1, MD_PERSIST_ON = 2, MD_PERSIST_CLUSTER = 3 };
-enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2, MD_SCHEDULE_TILES = 3,
-       MD_SCHEDULE_TABLE = 4 };
+enum { MD_PERSIST_AUTO = 0, MD_PERSIST_OFF = 1, MD_PERSIST_ON = 2 };
 
 /* Options.  Fill with md_options_default() and change what you need.
  *   precision        MD_PRECISION_FP64: all arithmetic in FP64.
@@ -107,57 +105,24 @@ enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2, MD_SCH
  *   block_size       threads per block of the per-atom kernels (0 = 256).
  *   lanes_per_atom   threads that share one atom's neighbour list in the
  *                    density and force passes: 1, 2, 4 or 8; 0 = chosen at
- *                    md_create by timing each (with the schedule and, for
- *                    the atom-parallel passes, threads per block) (the choice is kept for the
- *                    process, per precision and size class, so contexts of
- *                    the same shape follow the same schedule).  Results
- *                    depend on it only through FP summation order.
- *   schedule         MD_SCHEDULE_AUTO (0): chosen with lanes_per_atom when
- *                    that is 0 (timed), else MD_SCHEDULE_ATOMS.
- *                    MD_SCHEDULE_ATOMS: the density and force passes run one
- *                    atom per lanes_per_atom threads, neighbour records
- *                    gathered from device memory.
- *                    MD_SCHEDULE_ROWS: one block per row of cells (fixed y,
- *                    z cell index) stages the records of the 3 x 3 rows
- *                    around it in shared memory and gathers from there
- *                    (lanes_per_atom 1, 2 or 4).  Applies to one atom type
- *                    whose f and phi share a knot grid; otherwise, and for
- *                    any block whose rows outgrow the stage sized at
- *                    md_create, the atom-parallel gathers are used.  Forces
- *                    are bitwise those of MD_SCHEDULE_ATOMS with the same
- *                    lanes_per_atom; energy sums differ in rounding only.
- *                    MD_SCHEDULE_TILES: atom-parallel (lanes_per_atom 1, 2
- *                    or 4, one atom type with a shared knot grid), each
- *                    block first bulk-copies its atoms' list columns into
- *                    shared memory; results bitwise those of
- *                    MD_SCHEDULE_ATOMS.  A bulk copy that has not landed
- *                    within 1 s raises MD_ERR_TIMEOUT at the next md_sync.
- *                    MD_SCHEDULE_TABLE: mixed precision, one atom type with a
- *                    shared knot grid: persistent blocks (as many as fit on
- *                    the GPU at once) each copy the spline rows into shared
- *                    memory and walk tiles of atoms; lanes_per_atom 1, 2 or
- *                    4; forces bitwise those of MD_SCHEDULE_ATOMS.  Falls
- *                    back to MD_SCHEDULE_ATOMS where it does not apply.
+ *                    md_create by timing each together with the threads per
+ *                    block (the choice is kept for the process, per
+ *                    precision and size class, so contexts of the same shape
+ *                    follow the same schedule).  Each lane gathers its
+ *                    neighbours' records and spline rows from device memory.
+ *                    Results depend on it only through FP summation order.
  *   persistent       MD_PERSIST_AUTO (0): md_step runs as one launch (all
  *                    phases of all steps) for systems of at most 65,536
- *                    atoms, else as CUDA graphs.  The launch takes one of two
- *                    forms: a cooperative grid of all resident blocks
- *                    meeting at grid barriers in device memory, or (a few
- *                    thousand atoms: as many as the shared memory of 16 CTAs
- *                    holds) one thread-block cluster of at most 16 CTAs that
- *                    keep their atoms' state and lists in shared memory
- *                    between list builds, read neighbours through
- *                    distributed shared memory and meet at cluster
- *                    barriers.  MD_PERSIST_OFF: always the
+ *                    atoms, else as CUDA graphs.  The launch is a
+ *                    cooperative grid of all resident blocks meeting at grid
+ *                    barriers in device memory.  MD_PERSIST_OFF: always the
  *                    graph (or eager) path.  MD_PERSIST_ON: always the
- *                    cooperative grid.  MD_PERSIST_CLUSTER (3): always the
- *                    cluster (MD_ERR_CUDA at md_create if the system does
- *                    not fit one).  Form and lanes per atom: lanes_per_atom,
- *                    or timed at md_create over 1, 2, 4, 8 and the forms on
- *                    steps at dt = 0 (the state is restored).  Positions,
- *                    velocities and forces are bitwise those of the graph
- *                    path with the same lanes per atom; energy sums differ
- *                    in rounding only.  A barrier wait longer than 1 s ends
+ *                    single launch.  Lanes per atom: lanes_per_atom, or
+ *                    timed at md_create over 1, 2, 4, 8 on steps at dt = 0
+ *                    (the state is restored).  Positions, velocities and
+ *                    forces are bitwise those of the graph path with the
+ *                    same lanes per atom; energy sums differ in rounding
+ *                    only.  A barrier wait longer than the wait limit ends
  *                    the launch and raises MD_ERR_TIMEOUT.
  *   open_axes        one bit per open (non-periodic) axis: 1 = x, 2 = y,
  *                    4 = z; 0 = fully periodic.  The free-surface slabs of
@@ -171,12 +136,8 @@ enum { MD_SCHEDULE_AUTO = 0, MD_SCHEDULE_ATOMS = 1, MD_SCHEDULE_ROWS = 2, MD_SCH
  *                    inside the box for the FP32 accuracy bound of the mixed
  *                    path).  Batches are periodic only.
  *   wait_limit_us    longest device-side wait (a grid barrier of the single
- *                    launch, the bulk-copy barrier of list tiles) before the
- *                    kernel gives up and raises MD_ERR_TIMEOUT; 0 = 1 s.
- *   stage_capacity   records a row-staged block holds; 0 = 1.1 x the most
- *                    that any 3 x 3 block of rows holds at md_create, + 32.
- *                    Must fit the shared memory of a block (160 KB of
- *                    16-byte (mixed) or 32-byte (fp64) records).
+ *                    launch) before the kernel gives up and raises
+ *                    MD_ERR_TIMEOUT; 0 = 1 s.
  *   batch_schedule   batches only: 0 = threads per block and resident
  *                    blocks per SM timed at md_batch_create (unless
  *                    lanes_per_atom > 0, which takes 512 x 1); 1..5 =
@@ -192,8 +153,6 @@ typedef struct {
     void *(*alloc)(size_t bytes, void *alloc_ctx);
     void (*free)(void *ptr, void *alloc_ctx);
     void *alloc_ctx;
-    int32_t schedule;
-    int32_t stage_capacity;
     int32_t persistent;
     int32_t wait_limit_us;
     int32_t open_axes;
@@ -267,18 +226,10 @@ typedef struct {
     int64_t kernel_launches; /* kernels queued by this context so far */
     int32_t lanes_density;   /* lanes per atom of the density pass */
     int32_t lanes_force;     /* lanes per atom of the force pass */
-    int32_t rows_density;    /* 1: density pass row-staged (MD_SCHEDULE_ROWS) */
-    int32_t rows_force;      /* 1: force pass row-staged */
-    int32_t stage_capacity;  /* records a row-staged block holds (0: none) */
-    int32_t tiles_density;   /* 1: density pass list-tiled (MD_SCHEDULE_TILES) */
-    int32_t tiles_force;     /* 1: force pass list-tiled */
-    int32_t table_density;   /* 1: density pass with shared-memory spline rows */
-    int32_t table_force;     /* 1: force pass likewise */
     int32_t threads_density; /* threads per block of the density pass */
     int32_t threads_force;   /* threads per block of the force pass */
     int32_t persistent_blocks; /* blocks of the single-launch md_step (0: graphs) */
     int32_t persistent_lanes;  /* lanes per atom of its pair passes */
-    int32_t persistent_cluster; /* 1: the single launch is one cluster; 2: with the spline rows in shared memory */
 } md_stats_t;
 
 md_status md_stats(md_ctx *ctx, md_stats_t *out);

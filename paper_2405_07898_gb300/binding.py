@@ -24,8 +24,7 @@ STATUS = {0: "MD_OK", -1: "MD_ERR_ARG", -2: "MD_ERR_BOX", -3: "MD_ERR_CUDA", -4:
           -5: "MD_ERR_NONFINITE", -6: "MD_ERR_TIMEOUT", -7: "MD_ERR_LIST_OVERFLOW",
           -8: "MD_ERR_CAPACITY"}
 PRECISION = {"fp64": 0, "mixed": 1}
-PERSIST = {"auto": 0, "off": 1, "on": 2, "cluster": 3}
-SCHEDULE = {"auto": 0, "atoms": 1, "rows": 2, "tiles": 3, "table": 4}
+PERSIST = {"auto": 0, "off": 1, "on": 2}
 
 # every entry point declared in include/eammd.h
 EXPORTS = ("md_options_default", "md_create", "md_step", "md_sync", "md_energy", "md_forces",
@@ -55,8 +54,7 @@ class Options(C.Structure):
                 ("list_capacity", C.c_int32), ("use_graphs", C.c_int32),
                 ("block_size", C.c_int32), ("lanes_per_atom", C.c_int32),
                 ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", C.c_void_p), ("schedule", C.c_int32),
-                ("stage_capacity", C.c_int32),
+                ("alloc_ctx", C.c_void_p),
                 ("persistent", C.c_int32),
                 ("wait_limit_us", C.c_int32),
                 ("open_axes", C.c_int32),
@@ -67,12 +65,9 @@ class Stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("rebuilds", C.c_int64), ("max_neighbors", C.c_int32),
                 ("list_capacity", C.c_int32), ("table_out_of_range", C.c_int64),
                 ("kernel_launches", C.c_int64), ("lanes_density", C.c_int32),
-                ("lanes_force", C.c_int32), ("rows_density", C.c_int32),
-                ("rows_force", C.c_int32), ("stage_capacity", C.c_int32), ("tiles_density", C.c_int32),
-                ("tiles_force", C.c_int32), ("table_density", C.c_int32),
-                ("table_force", C.c_int32), ("threads_density", C.c_int32),
+                ("lanes_force", C.c_int32), ("threads_density", C.c_int32),
                 ("threads_force", C.c_int32), ("persistent_blocks", C.c_int32),
-                ("persistent_lanes", C.c_int32), ("persistent_cluster", C.c_int32)]
+                ("persistent_lanes", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -225,8 +220,8 @@ class MD:
 
     def __init__(self, system, precision: str = "mixed", rebuild_every: int = 10,
                  list_capacity: int = 0, use_graphs: bool = True, block_size: int = 256,
-                 lanes_per_atom: int = 0, use_torch: bool | None = None, schedule: str = "auto",
-                 stage_capacity: int = 0, persistent: str = "auto", wait_limit_us: int = 0):
+                 lanes_per_atom: int = 0, use_torch: bool | None = None, persistent: str = "auto",
+                 wait_limit_us: int = 0):
         L = load()
         self._L = L
         self.n = int(system.n)
@@ -239,8 +234,6 @@ class MD:
         opt.use_graphs = 1 if use_graphs else 0
         opt.block_size = block_size
         opt.lanes_per_atom = lanes_per_atom
-        opt.schedule = SCHEDULE[schedule]
-        opt.stage_capacity = stage_capacity
         opt.persistent = PERSIST[persistent]
         opt.wait_limit_us = wait_limit_us
         opt.open_axes = int(getattr(system, "open_axes", 0))

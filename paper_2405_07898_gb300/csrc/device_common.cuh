@@ -141,12 +141,6 @@ __device__ __forceinline__ Shift<float> entry_shift<float>(uint32_t e, const flo
     const float mz = __uint_as_float((c >> 4) | 0x4B400000u) - 12582913.0f;
     return Shift<float>{mx * h[0], my * h[1], mz * h[2]};
 }
-// Row (dz + 1) * 3 + (dy + 1) of the 3 x 3 rows of cells around an atom's
-// row that a list entry's neighbour lives in.
-__device__ __forceinline__ int entry_row(uint32_t e)
-{
-    return (int)(e >> (kCodeShift + 4)) * 3 + (int)((e >> (kCodeShift + 2)) & 3u);
-}
 template <class R>
 __device__ __forceinline__ void load_h(const Geom &G, R (&h)[3])
 {

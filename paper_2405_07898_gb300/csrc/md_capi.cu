@@ -3,7 +3,6 @@
 // whose list rebuild sits in a device-side conditional node), and the
 // marshalling of states between the caller's order and the sorted order.
 #include "eammd.h"
-#include "cluster.cuh"
 #include "md_internal.cuh"
 #include "spline_host.h"
 
@@ -101,9 +100,6 @@ struct md_ctx {
     // persistent step launch (md_step as one cooperative kernel)
     PersistScratch *ps = nullptr;
     int persist_tpa = 0, persist_grid = 0;  // 0: graph path
-    int persist_cluster = 0;                // 1: the single launch is one cluster; 2: with shared tables
-    ClusterPlan persist_plan{0, 0, 0};
-    int persist_cap = 0;                    // list capacity the cluster plan was made for
     std::string err;
 
     md_status fail(md_status s, const std::string &m)
@@ -441,24 +437,12 @@ template <class R> md_status setup_persistent(md_ctx *ctx);
 template <class R>
 md_status step_impl(md_ctx *ctx, int64_t nsteps, double dt)
 {
-    // the cluster form holds the list columns in shared memory: a capacity
-    // grown since it was planned (by md_set_state) needs a new plan
-    if (ctx->persist_cluster > 0 && ctx->persist_cap != ctx->L.cap) {
-        md_status rc = setup_persistent<R>(ctx);
-        if (rc != MD_OK) return rc;
-    }
     const Bufs<R> &B = bufs<R>(ctx);
     ctx->L.dt = dt;
     for (int t = 0; t < ctx->ntypes; ++t) ctx->L.half_kick[t] = 0.5 * dt * kAccel / ctx->mass[t];
     Launch L = ctx->L;
     L.use_cond = 0;
     L.cond = 0;
-    if (ctx->persist_cluster > 0) {
-        CK(launch_steps_cluster<R>(B, ctx->G, L, nsteps, ctx->persist_tpa, ctx->persist_cluster == 2,
-                                   ctx->persist_plan, ctx->ps));
-        ctx->fixed_launches += 1;
-        return MD_OK;
-    }
     if (ctx->persist_grid > 0) {
         CK(launch_steps<R>(B, ctx->G, L, nsteps, ctx->persist_tpa, ctx->persist_grid, ctx->ps));
         ctx->fixed_launches += 1;
@@ -614,10 +598,9 @@ md_status build_tables(md_ctx *ctx, const md_potential *pot, std::vector<double>
     return MD_OK;
 }
 
-// Schedule of one pass: lanes per atom and where its gathers read from.
-enum SchedKind { SCHED_ATOMS = 0, SCHED_ROWS = 1, SCHED_TILES = 2, SCHED_TABLE = 3 };
+// Schedule of one pass: lanes per atom and threads per block.
 struct PassSched {
-    int tpa, kind, block;  // block 0: the context's block_size
+    int tpa, block;  // block 0: the context's block_size
 };
 
 void set_sched(md_ctx *ctx, PassSched d, PassSched f)
@@ -625,31 +608,10 @@ void set_sched(md_ctx *ctx, PassSched d, PassSched f)
     Launch &L = ctx->L;
     L.tpa_d = d.tpa;
     L.tpa_f = f.tpa;
-    L.staged_d = d.kind == SCHED_ROWS;
-    L.staged_f = f.kind == SCHED_ROWS;
-    L.tiled_d = d.kind == SCHED_TILES;
-    L.tiled_f = f.kind == SCHED_TILES;
-    L.tab_d = d.kind == SCHED_TABLE;
-    L.tab_f = f.kind == SCHED_TABLE;
     L.block_d = d.block > 0 ? d.block : L.block;
     L.block_f = f.block > 0 ? f.block : L.block;
-    L.nb_d = L.staged_d ? L.nrows
-                        : (L.tab_d ? table_grid(L, false, d.tpa, L.block_d)
-                                   : blocks_for_host((int64_t)L.n * d.tpa, L.block_d));
-    L.nb_f = L.staged_f ? L.nrows
-                        : (L.tab_f ? table_grid(L, true, f.tpa, L.block_f)
-                                   : blocks_for_host((int64_t)L.n * f.tpa, L.block_f));
-}
-
-// Whether the shared-table passes can run: FP32 pair arithmetic, fused
-// tables, rows that fit the shared memory of a block, and at least one
-// resident block.
-bool table_usable(md_ctx *ctx, int tpa)
-{
-    const Launch &L = ctx->L;
-    return ctx->precision == MD_PRECISION_MIXED && !L.multi && L.nint_fused > 0 &&
-           table_smem_bytes(L, true) <= (size_t)kSharedLimitBytes && table_grid(L, true, tpa, L.block) > 0 &&
-           table_grid(L, false, tpa, L.block) > 0;
+    L.nb_d = blocks_for_host((int64_t)L.n * d.tpa, L.block_d);
+    L.nb_f = blocks_for_host((int64_t)L.n * f.tpa, L.block_f);
 }
 
 // Choices of the autotuner, per (precision, type path, size bucket), kept for
@@ -663,50 +625,6 @@ struct TuneChoice {
 };
 std::mutex g_tune_mu;
 std::vector<std::pair<TuneKey, TuneChoice>> g_tune_cache;
-
-// Stage capacity of the row-staged passes from the cell occupancy of the
-// current list build: the most records any 3 x 3 block of rows holds, with
-// room for atoms that change cells at later builds.  Blocks that outgrow it
-// gather from device memory.  0 when rows staging does not apply.
-template <class R>
-md_status setup_staging(md_ctx *ctx)
-{
-    Launch &L = ctx->L;
-    L.stage_cap = 0;
-    const md_options &o = ctx->opt;
-    if (L.multi || ctx->n == 0) return MD_OK;
-    // the attribute only permits the shared memory; occupancy follows what a
-    // launch asks for
-    CK(allow_shared_staging<R>(kSharedLimitBytes));
-    const bool wanted = o.schedule == MD_SCHEDULE_ROWS || (o.schedule == MD_SCHEDULE_AUTO && o.lanes_per_atom == 0);
-    if (!wanted) return MD_OK;
-    const Geom &G = ctx->G;
-    const int nx = G.ncell[0], ny = G.ncell[1], nz = G.ncell[2];
-    std::vector<int> cs((size_t)G.ncells + 1);
-    CK(cudaMemcpyAsync(cs.data(), bufs<R>(ctx).cell_start, sizeof(int) * cs.size(), cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    int64_t most = 0;
-    for (int cz = 0; cz < nz; ++cz)
-        for (int cy = 0; cy < ny; ++cy) {
-            int64_t sum = 0;
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy) {
-                    const int ey = (cy + dy + ny) % ny, ez = (cz + dz + nz) % nz;
-                    const int r = ez * ny + ey;
-                    sum += cs[(size_t)(r + 1) * nx] - cs[(size_t)r * nx];
-                }
-            most = std::max(most, sum);
-        }
-    const int64_t cap = o.stage_capacity > 0 ? (int64_t)o.stage_capacity
-                                             : ((int64_t)std::ceil(1.1 * (double)most) + 32 + 31) / 32 * 32;
-    if (cap * (int64_t)sizeof(typename V4<R>::T) > kSharedLimitBytes) {
-        if (o.stage_capacity > 0) return ctx->fail(MD_ERR_ARG, "stage_capacity exceeds the shared memory of a block");
-        return MD_OK;
-    }
-    L.stage_cap = (int)cap;
-    return MD_OK;
-}
 
 // Density and force (forces only, no integration) at the current state.
 template <class R>
@@ -724,27 +642,19 @@ md_status reevaluate(md_ctx *ctx)
 
 // Schedule of the density and force passes: time, on the current state
 // (density, and the force pass with its kicks and drift at dt = 0; neither
-// changes positions or velocities), the atom-parallel passes with 1, 2, 4, 8 lanes per atom
-// gathering the list from device memory, and, on the one-type path, with 1,
-// 2, 4 lanes from a shared-memory list tile and row-staged with 1, 2, 4
-// (where a stage was sized); keep the fastest of each pass.
+// changes positions or velocities), the atom-parallel passes with 1, 2, 4, 8
+// lanes per atom and several block sizes; keep the fastest of each pass.
 template <class R>
 md_status autotune(md_ctx *ctx)
 {
     int bucket = 0;
     for (int64_t m = ctx->n; m > 1; m >>= 1) ++bucket;
     TuneKey key{ctx->precision, ctx->L.multi, bucket};
-    auto usable = [&](const PassSched &p) {
-        return (p.kind != SCHED_ROWS || ctx->L.stage_cap > 0) && (p.kind != SCHED_TABLE || table_usable(ctx, p.tpa));
-    };
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         for (auto &e : g_tune_cache)
             if (e.first.precision == key.precision && e.first.multi == key.multi && e.first.bucket == key.bucket) {
-                PassSched d = e.second.d, f = e.second.f;
-                if (!usable(d)) d = {d.tpa, SCHED_ATOMS, d.block};
-                if (!usable(f)) f = {f.tpa, SCHED_ATOMS, f.block};
-                set_sched(ctx, d, f);
+                set_sched(ctx, e.second.d, e.second.f);
                 return reevaluate<R>(ctx);
             }
     }
@@ -753,17 +663,9 @@ md_status autotune(md_ctx *ctx)
     // wave of blocks on the GPU
     std::vector<PassSched> cand;
     for (int t : {1, 2})
-        for (int b : {256, 224, 192, 160, 128, 96, 64}) cand.push_back({t, SCHED_ATOMS, b});
-    cand.push_back({4, SCHED_ATOMS, 256});
-    cand.push_back({8, SCHED_ATOMS, 256});
-    if (!ctx->L.multi) {
-        for (int t : {1, 2, 4})
-            if (list_tile_bytes(ctx->L, t, 256) <= (size_t)kSharedLimitBytes) cand.push_back({t, SCHED_TILES, 256});
-        if (ctx->L.stage_cap > 0)
-            for (int t : {1, 2, 4}) cand.push_back({t, SCHED_ROWS, 256});
-        for (int t : {1, 2, 4})
-            if (table_usable(ctx, t)) cand.push_back({t, SCHED_TABLE, 256});
-    }
+        for (int b : {256, 224, 192, 160, 128, 96, 64}) cand.push_back({t, b});
+    cand.push_back({4, 256});
+    cand.push_back({8, 256});
     const int nc = (int)cand.size();
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -829,21 +731,16 @@ md_status autotune(md_ctx *ctx)
 // graph replay (measured on GB300 over the BCC sweep).
 constexpr int64_t kPersistentAutoAtoms = 65536;
 
-// The persistent step launch.  Forms: a cooperative grid of as many blocks as
-// are resident (any size), or one thread-block cluster whose CTAs keep their
-// atoms' state and lists in shared memory (as many atoms as kMaxClusterCtas
-// CTAs hold), optionally with the FP32 spline rows there too.  Lanes per atom come
-// from the options, else every feasible (form, lanes) pair is timed over
-// rebuild_every - 1 steps at dt = 0, which moves no atom and builds no list;
-// the device state is restored after each trial.
+// The persistent step launch: a cooperative grid of as many blocks as are
+// resident.  Lanes per atom come from the options, else every feasible
+// choice is timed over rebuild_every - 1 steps at dt = 0, which moves no atom
+// and builds no list; the device state is restored after each trial.
 template <class R>
 md_status setup_persistent(md_ctx *ctx)
 {
     ctx->persist_grid = 0;
-    ctx->persist_cluster = 0;
     const md_options &o = ctx->opt;
-    const bool want = o.persistent == MD_PERSIST_ON || o.persistent == MD_PERSIST_CLUSTER ||
-                      (o.persistent == MD_PERSIST_AUTO && ctx->n <= kPersistentAutoAtoms);
+    const bool want = o.persistent == MD_PERSIST_ON || (o.persistent == MD_PERSIST_AUTO && ctx->n <= kPersistentAutoAtoms);
     if (!want || ctx->n == 0) return MD_OK;
     const bool forced = o.persistent != MD_PERSIST_AUTO;
     if (!ctx->ps) {
@@ -859,25 +756,13 @@ md_status setup_persistent(md_ctx *ctx)
     else if (ctx->L.rebuild_every < 2) tpas.push_back(2);  // every step builds: no state-neutral trial
     else tpas = {1, 2, 4, 8};
     struct Cand {
-        int tpa, grid, cluster;
-        ClusterPlan plan;
+        int tpa, grid;
     };
     std::vector<Cand> cand;
     for (int tpa : tpas) {
-        if (o.persistent != MD_PERSIST_CLUSTER && coop) {
-            const int grid = persistent_grid<R>(ctx->L, tpa);
-            if (grid > 0) cand.push_back({tpa, grid, 0, {0, 0, 0}});
-        }
-        if (o.persistent != MD_PERSIST_ON) {
-            // schedule ATOMS: records only in shared memory; TABLE: the
-            // spline rows too; otherwise both are timed
-            const int f0 = o.schedule == MD_SCHEDULE_TABLE ? 2 : 1, f1 = o.schedule == MD_SCHEDULE_ATOMS ? 1 : 2;
-            for (int form = f0; form <= f1; ++form) {
-                ClusterPlan plan{0, 0, 0};
-                const int nF = ctx->shapes.empty() ? 0 : ctx->shapes[0].n - 1;  // F of type 0
-                if (cluster_plan<R>(ctx->L, tpa, form == 2, nF, plan)) cand.push_back({tpa, plan.nct, form, plan});
-            }
-        }
+        if (!coop) break;
+        const int grid = persistent_grid<R>(ctx->L, tpa);
+        if (grid > 0) cand.push_back({tpa, grid});
     }
     if (cand.empty()) {
         if (forced) return ctx->fail(MD_ERR_CUDA, "the persistent step kernel cannot be resident");
@@ -885,10 +770,7 @@ md_status setup_persistent(md_ctx *ctx)
     }
     auto take = [&](const Cand &c) {
         ctx->persist_tpa = c.tpa;
-        ctx->persist_cluster = c.cluster;
-        ctx->persist_plan = c.plan;
-        ctx->persist_cap = ctx->L.cap;
-        ctx->persist_grid = c.cluster ? 0 : c.grid;
+        ctx->persist_grid = c.grid;
     };
     if (cand.size() == 1 || ctx->L.rebuild_every < 2) {
         take(cand[0]);
@@ -910,8 +792,7 @@ md_status setup_persistent(md_ctx *ctx)
         for (size_t c = 0; c < cand.size(); ++c) {
             const Cand &k = cand[c];
             CK(cudaEventRecord(e0, ctx->stream));
-            if (k.cluster) CK(launch_steps_cluster<R>(B, ctx->G, L, trial_steps, k.tpa, k.cluster == 2, k.plan, ctx->ps));
-            else CK(launch_steps<R>(B, ctx->G, L, trial_steps, k.tpa, k.grid, ctx->ps));
+            CK(launch_steps<R>(B, ctx->G, L, trial_steps, k.tpa, k.grid, ctx->ps));
             CK(cudaEventRecord(e1, ctx->stream));
             CK(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -1102,27 +983,8 @@ md_status create_impl(md_ctx *ctx, const double *pos, const double *vel, const i
     CK(cudaMemcpy(ctx->types_orig, types, sizeof(int32_t) * (size_t)ctx->n, cudaMemcpyHostToDevice));
     md_status rc = load_and_measure<R>(ctx, pos, vel, 0);
     if (rc != MD_OK) return rc;
-    rc = setup_staging<R>(ctx);
-    if (rc != MD_OK) return rc;
     const md_options &o = ctx->opt;
-    const int forced_lanes = o.lanes_per_atom > 0 ? o.lanes_per_atom : 2;
-    const bool forced = (o.schedule == MD_SCHEDULE_ROWS || o.schedule == MD_SCHEDULE_TILES) ||
-                        (o.schedule == MD_SCHEDULE_TABLE && table_usable(ctx, forced_lanes));
-    if (forced && !ctx->L.multi) {
-        const int lanes = forced_lanes;
-        const PassSched p{lanes,
-                          o.schedule == MD_SCHEDULE_ROWS    ? SCHED_ROWS
-                          : o.schedule == MD_SCHEDULE_TILES ? SCHED_TILES
-                                                            : SCHED_TABLE,
-                          0};
-        set_sched(ctx, p, p);
-        rc = reevaluate<R>(ctx);
-        if (rc != MD_OK) return rc;
-        rc = check_device_errors(ctx);
-        if (rc != MD_OK) return rc;
-        return setup_persistent<R>(ctx);
-    }
-    if (o.lanes_per_atom == 0 && o.schedule == MD_SCHEDULE_AUTO) {
+    if (o.lanes_per_atom == 0) {
         rc = autotune<R>(ctx);
         if (rc != MD_OK) return rc;
     }
@@ -1204,13 +1066,8 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     if (!(o.lanes_per_atom == 0 || o.lanes_per_atom == 1 || o.lanes_per_atom == 2 || o.lanes_per_atom == 4 ||
           o.lanes_per_atom == 8))
         return bad(MD_ERR_ARG, "lanes_per_atom must be 0 (tune), 1, 2, 4 or 8");
-    if (o.schedule < MD_SCHEDULE_AUTO || o.schedule > MD_SCHEDULE_TABLE)
-        return bad(MD_ERR_ARG, "schedule must be MD_SCHEDULE_AUTO, _ATOMS, _ROWS, _TILES or _TABLE");
-    if (o.schedule >= MD_SCHEDULE_ROWS && o.lanes_per_atom == 8)
-        return bad(MD_ERR_ARG, "row-staged, list-tiled and shared-table passes take 1, 2 or 4 lanes per atom");
-    if (o.stage_capacity < 0) return bad(MD_ERR_ARG, "stage_capacity must be >= 0");
-    if (o.persistent < MD_PERSIST_AUTO || o.persistent > MD_PERSIST_CLUSTER)
-        return bad(MD_ERR_ARG, "persistent must be MD_PERSIST_AUTO, _OFF, _ON or _CLUSTER");
+    if (o.persistent < MD_PERSIST_AUTO || o.persistent > MD_PERSIST_ON)
+        return bad(MD_ERR_ARG, "persistent must be MD_PERSIST_AUTO, _OFF or _ON");
     if (o.wait_limit_us < 0) return bad(MD_ERR_ARG, "wait_limit_us must be >= 0");
 
     md_ctx *ctx = new (std::nothrow) md_ctx();
@@ -1269,17 +1126,16 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     L.block = o.block_size;
     L.nblocks = (int)((n + L.block - 1) / L.block);
     {
-        // the list build of a small system: blocks as small as it takes to
-        // give every SM two (down to one warp)
+        // the list build (one warp per cell) of a small system: as few cells
+        // per block as it takes to give every SM two blocks (down to one)
         int dev = 0, nsm = 152;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             nsm = 152;
-        L.list_block = L.block;
-        while (L.list_block > 32 && (n + L.list_block - 1) / L.list_block < 2 * (int64_t)nsm) L.list_block /= 2;
-        L.list_block = std::max(32, L.list_block / 32 * 32);
+        int wpb = kListWarps;
+        while (wpb > 1 && ((int64_t)G.ncells + wpb - 1) / wpb < 2 * (int64_t)nsm) wpb /= 2;
+        L.list_block = 32 * wpb;
     }
-    L.nrows = G.ncell[1] * G.ncell[2];
-    L.pstride = std::max({1, blocks_for_host(8 * n, std::min(L.block, 128)), L.nrows});
+    L.pstride = std::max(1, blocks_for_host(8 * n, std::min(L.block, 128)));
     {
         int lanes = o.lanes_per_atom > 0 ? o.lanes_per_atom : 4;
         L.tpa_d = L.tpa_f = lanes;
@@ -1463,18 +1319,10 @@ md_status md_stats(md_ctx *ctx, md_stats_t *out)
     out->kernel_launches = ctx->fixed_launches + 8 * h.graph_rebuilds;
     out->lanes_density = ctx->L.tpa_d;
     out->lanes_force = ctx->L.tpa_f;
-    out->rows_density = ctx->L.staged_d;
-    out->rows_force = ctx->L.staged_f;
-    out->tiles_density = ctx->L.tiled_d;
-    out->tiles_force = ctx->L.tiled_f;
-    out->table_density = ctx->L.tab_d;
-    out->table_force = ctx->L.tab_f;
     out->threads_density = ctx->L.block_d;
     out->threads_force = ctx->L.block_f;
-    out->persistent_blocks = ctx->persist_cluster ? ctx->persist_plan.nct : ctx->persist_grid;
-    out->persistent_lanes = (ctx->persist_cluster || ctx->persist_grid) ? ctx->persist_tpa : 0;
-    out->persistent_cluster = ctx->persist_cluster;
-    out->stage_capacity = ctx->L.stage_cap;
+    out->persistent_blocks = ctx->persist_grid;
+    out->persistent_lanes = ctx->persist_grid ? ctx->persist_tpa : 0;
     return MD_OK;
 }
 

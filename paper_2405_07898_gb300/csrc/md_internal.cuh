@@ -39,6 +39,7 @@ __host__ __device__ constexpr uint32_t list_entry(uint32_t q, int dx, int dy, in
     return q | ((uint32_t)((dx + 1) | ((dy + 1) << 2) | ((dz + 1) << 4)) << kCodeShift);
 }
 constexpr int kScanBlock = 1024;
+constexpr int kListWarps = 8;  // most cells (warps) per block of the list build
 constexpr int kEnergySlots = 10;  // embed, pair, ke, virial xx yy zz xy xz yz, spare
 constexpr double kAccel = 9.648533215665e-3;  // (eV/Angstrom/amu) -> Angstrom/fs^2
 
@@ -143,7 +144,7 @@ struct Launch {
     int ld;         // list leading dimension (multiple of 32)
     int cap;        // list slots per atom
     int block;      // threads per block of per-atom kernels
-    int list_block; // threads per block of the list build (smaller for small systems, to fill the SMs)
+    int list_block; // threads per block of the list build: one warp per cell, fewer cells per block for small systems
     int block_d;    // threads per block of the density pass
     int block_f;    // threads per block of the force pass
     int nblocks;    // ceil(n / block)
@@ -151,16 +152,8 @@ struct Launch {
     int tpa_f;      // lanes per atom of the force pass
     int nb_d;       // blocks of the density pass
     int nb_f;       // blocks of the force pass
-    int pstride;    // stride between energy slots in partials (>= nb_d, nb_f, nrows)
+    int pstride;    // stride between energy slots in partials (>= nb_d, nb_f)
     int nint_fused; // intervals of the fused f|phi table (0: not fused)
-    int nrows;      // rows of cells (ncell[1] * ncell[2]): blocks of a row-staged pass
-    int stage_cap;  // neighbour records one row-staged block stages (0: none)
-    int staged_d;   // density pass row-staged
-    int staged_f;   // force pass row-staged
-    int tiled_d;    // density pass (atom-parallel) reads its list tile from shared memory
-    int tiled_f;    // force pass likewise
-    int tab_d;      // density pass (FP32, one type) with its spline rows in shared memory, persistent grid
-    int tab_f;      // force pass likewise
     int multi;      // general type-dependent path (several types or unfused tables)
     int ntypes;
     int rebuild_every;
@@ -199,28 +192,6 @@ template <class R>
 cudaError_t launch_steps(const Bufs<R> &B, const Geom &G, const Launch &L, long long nsteps, int tpa, int grid,
                          PersistScratch *ps);
 
-// Opt the row-staged and list-tiled passes in to `bytes` of dynamic shared
-// memory.
-template <class R> cudaError_t allow_shared_staging(int bytes);
-
-// Dynamic shared memory a row-staged or list-tiled block may ask for.
-constexpr int kSharedLimitBytes = 160 * 1024;
-
-// Shared memory of a shared-table block: the f rows (density) or the f and
-// phi rows (force) of the fused FP32 table.
-inline size_t table_smem_bytes(const Launch &L, bool force)
-{
-    return (size_t)L.nint_fused * 16u * (force ? 2u : 1u);
-}
-// Grid of a shared-table pass of `block` threads: the blocks that fit on the
-// GPU at once (0 if none fit).  pair_f32.cu.
-int table_grid(const Launch &L, bool force, int tpa, int block);
-
-// Shared memory of a list-tiled block: its atoms' list columns.
-inline size_t list_tile_bytes(const Launch &L, int tpa, int block)
-{
-    return (size_t)(block / tpa) * (size_t)L.cap * sizeof(uint32_t);
-}
 template <class R> int launch_reduce(const Bufs<R> &B, const Launch &L);
 template <class R>
 int launch_load_state(const Bufs<R> &B, const Launch &L, const double *pos, const double *vel, const int *types);

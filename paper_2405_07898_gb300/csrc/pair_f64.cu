@@ -4,5 +4,4 @@
 namespace eammd {
 template int launch_density<double>(const Bufs<double> &, const Geom &, const Launch &, bool);
 template int launch_force<double>(const Bufs<double> &, const Geom &, const Launch &, int, bool);
-template cudaError_t allow_shared_staging<double>(int);
 }  // namespace eammd

@@ -1,19 +1,11 @@
 // pair_kernels.cuh -- the density and force passes of the EAM timestep.
 //
-// Two schedules share the per-atom work:
-//   * atom-parallel (k_density, k_force): TPA lanes cooperate on one atom;
-//     lane l walks list columns l, l+TPA, ... a few at a time (every gather
-//     of a round issued before any is used: three pairs a round in the
-//     density pass, two in the force pass with the next round in flight),
-//     the lanes' sums meet by warp shuffles; neighbour records are gathered
-//     from global memory;
-//   * row-staged (k_density_rows, k_force_rows): one block per row of cells
-//     (all cx for a fixed cy, cz) first copies the records of the 3 x 3 rows
-//     around it -- every neighbour its atoms can have -- into shared memory
-//     with coalesced loads, then gathers from there.  A list entry's stencil
-//     code names the row its neighbour lives in, so the shared-memory slot is
-//     the neighbour's index minus that row's base.  Blocks whose neighbourhood
-//     exceeds the staging capacity gather from global memory instead.
+// Atom-parallel schedule (k_density, k_force): TPA lanes cooperate on one
+// atom; lane l walks list columns l, l+TPA, ... a few at a time (every
+// gather of a round issued before any is used: three pairs a round in the
+// density pass, two in the force pass with the next round in flight), and
+// the lanes' sums meet by warp shuffles.  Neighbour records and spline rows
+// are gathered from global memory through L1.
 // The neighbour record is the 16-byte shadow (u_x, u_y, u_z, F'_j): one
 // gather gives the force pass both the position and the embedding derivative
 // the density pass stored.  With one atom type whose f and phi share a knot
@@ -76,22 +68,10 @@ struct GlobalFetch {
     __device__ __forceinline__ typename V4<R>::T operator()(uint32_t e) const { return sw[e & kIndexMask]; }
 };
 
-template <class R>
-struct StagedFetch {
-    const typename V4<R>::T *stage;
-    const int *base;  // per neighbour row (entry_row): first atom index minus its stage offset
-    __device__ __forceinline__ typename V4<R>::T operator()(uint32_t e) const
-    {
-        return stage[(int)(e & kIndexMask) - base[entry_row(e)]];
-    }
-};
-
 // Where the spline rows of the one-type path are read from: coef2 in device
-// memory (row 2k: f, row 2k+1: phi, both in one 32-byte load; the density
+// memory (row 2k: f, row 2k+1: phi, both in one 32-byte load); the density
 // pass reads the f rows alone from coef_f, where a 128-byte line holds eight
-// intervals instead of four) or a copy in shared memory with the f and phi
-// rows in two arrays, so that 16-byte reads at scattered rows spread over
-// all banks.
+// intervals instead of four.
 template <class R>
 struct TabGlobal {
     const typename V4<R>::T *coef2;
@@ -102,87 +82,17 @@ struct TabGlobal {
         load_row2<R>(coef2 + 2 * kk, cf, cp);
     }
 };
-struct TabShared {
-    const float4 *f_rows, *phi_rows;
-    __device__ __forceinline__ float4 f(int kk) const { return f_rows[kk]; }
-    __device__ __forceinline__ void fphi(int kk, float4 &cf, float4 &cp) const
-    {
-        cf = f_rows[kk];
-        cp = phi_rows[kk];
-    }
-};
-
 // Where list column k of the lane's atom is read from.
 struct ListGlobal {
     const uint32_t *lp;  // list + i
     int ld;
     __device__ __forceinline__ uint32_t operator()(int k) const { return lp[(size_t)k * ld]; }
 };
-struct ListTile {
-    const uint32_t *tp;  // tile + (i - i0)
-    int width;           // atoms per tile column
-    __device__ __forceinline__ uint32_t operator()(int k) const { return tp[k * width]; }
-};
-
 __device__ __forceinline__ uint64_t global_ns()
 {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
-}
-
-// Wait for phase `parity` of an mbarrier for at most limit_ns.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns)
-{
-    const uint64_t t0 = global_ns();
-    for (;;) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (global_ns() - t0 > limit_ns) return false;
-    }
-}
-
-constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s: for copies still in flight after a timeout
-
-// Columns 0 .. ncol-1 of the list of atoms [i0, i0 + width) into the block's
-// tile (column k at tile + k * width) by bulk asynchronous copies, one per
-// column, that complete on one mbarrier.  Every column is a contiguous,
-// 128-byte aligned run of the list (ld and width are multiples of 32 atoms).
-// Returns false (and flags ERR_TIMEOUT) if the copies did not land within
-// wait_ns; the caller then reads the list from device memory.
-__device__ __forceinline__ bool stage_list(const uint32_t *list, int ld, int i0, int width, int ncol,
-                                           uint32_t *tile, unsigned int *err, uint64_t wait_ns)
-{
-    __shared__ __align__(8) uint64_t bar;
-    const uint32_t bar_a = (uint32_t)__cvta_generic_to_shared(&bar);
-    const int w = min(width, ld - i0);
-    const uint32_t col_bytes = (uint32_t)w * 4u;
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(col_bytes * (uint32_t)ncol)
-                     : "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        for (int k = threadIdx.x; k < ncol; k += 32) {
-            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(tile + (size_t)k * width);
-            const uint32_t *src = list + (size_t)k * ld + i0;
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                "l"(src), "r"(col_bytes), "r"(bar_a)
-                : "memory");
-        }
-    }
-    if (mbar_wait(bar_a, 0, wait_ns)) return true;
-    atomicOr(err, ERR_TIMEOUT);
-    mbar_wait(bar_a, 0, kWaitLimitNs);  // the copies still own the tile
-    return false;
 }
 
 // This lane's part of rho_i = sum over listed j with r < r_cut of f_{t_j}(r_ij)
@@ -428,12 +338,7 @@ template <bool MULTI> struct PairsInFlight {
     static constexpr int force = 2;
 };
 
-extern __shared__ __align__(32) unsigned char dyn[];
-
-// LS: the block's list tile is brought into shared memory by bulk copies
-// first (one-type path only), so that the lanes' gathers do not wait on the
-// list stream.
-template <class R, bool MULTI, bool ENERGY, int TPA, bool LS>
+template <class R, bool MULTI, bool ENERGY, int TPA>
 __global__ void __launch_bounds__(256) k_density(Bufs<R> B, Geom G, Launch L)
 {
     using R4 = typename V4<R>::T;
@@ -445,22 +350,15 @@ __global__ void __launch_bounds__(256) k_density(Bufs<R> B, Geom G, Launch L)
     R4 *sw = B.shadow[sp];
     const int width = blockDim.x / TPA;
     const int i0 = blockIdx.x * width;
-    uint32_t *tile = reinterpret_cast<uint32_t *>(dyn);
-    if (!LS) prefetch_warp_streams<R, false>(B, L, s, i0 + (threadIdx.x >> 5) * (32 / TPA), 32 / TPA, min(st->max_nnb, L.cap));
-    const bool tiled = LS && stage_list(B.list, L.ld, i0, width, min(st->max_nnb, L.cap), tile, &B.st->error, L.wait_ns);
+    prefetch_warp_streams<R, false>(B, L, s, i0 + (threadIdx.x >> 5) * (32 / TPA), 32 / TPA, min(st->max_nnb, L.cap));
     const int i = i0 + threadIdx.x / TPA, l = threadIdx.x % TPA;
     const bool active = i < L.n;
     const int ti = (MULTI && active) ? B.type[s][i] : 0;
     const R rc2 = g_rc2<R>(G);
     R rho = (R)0;
-    if (active) {
-        if (tiled)
-            rho = density_lane<R, MULTI, TPA, U>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], ListTile{tile + (i - i0), width},
-                                                 GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2, B.coef_f});
-        else
-            rho = density_lane<R, MULTI, TPA, U>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], ListGlobal{B.list + i, L.ld},
-                                                 GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2, B.coef_f});
-    }
+    if (active)
+        rho = density_lane<R, MULTI, TPA, U>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], ListGlobal{B.list + i, L.ld},
+                                             GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2, B.coef_f});
     rho = lane_sum<TPA>(rho);
     R e_embed = (R)0;
     if (active && l == 0) e_embed = embed<R>(B, sw, i, ti, rho);
@@ -470,7 +368,7 @@ __global__ void __launch_bounds__(256) k_density(Bufs<R> B, Geom G, Launch L)
     }
 }
 
-template <class R, bool MULTI, int MODE, bool ENERGY, int TPA, bool LS>
+template <class R, bool MULTI, int MODE, bool ENERGY, int TPA>
 __global__ void __launch_bounds__(256) k_force(Bufs<R> B, Geom G, Launch L)
 {
     using R4 = typename V4<R>::T;
@@ -482,23 +380,16 @@ __global__ void __launch_bounds__(256) k_force(Bufs<R> B, Geom G, Launch L)
     const R4 *sw = B.shadow[sp];
     const int width = blockDim.x / TPA;
     const int i0 = blockIdx.x * width;
-    uint32_t *tile = reinterpret_cast<uint32_t *>(dyn);
-    prefetch_warp_streams<R, true>(B, L, s, i0 + (threadIdx.x >> 5) * (32 / TPA), 32 / TPA, LS ? 0 : min(st->max_nnb, L.cap));
-    const bool tiled = LS && stage_list(B.list, L.ld, i0, width, min(st->max_nnb, L.cap), tile, &B.st->error, L.wait_ns);
+    prefetch_warp_streams<R, true>(B, L, s, i0 + (threadIdx.x >> 5) * (32 / TPA), 32 / TPA, min(st->max_nnb, L.cap));
     const int i = i0 + threadIdx.x / TPA, l = threadIdx.x % TPA;
     const bool active = i < L.n;
     const int ti = (MULTI && active) ? B.type[s][i] : 0;
     const R rc2 = g_rc2<R>(G);
     R f[3] = {0, 0, 0};
     R e7[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (active) {
-        if (tiled)
-            force_lane<R, MULTI, ENERGY, TPA, U>(B, L, h, rc2, s, B.nnb + i, l, ti, sw[i], ListTile{tile + (i - i0), width},
-                                                 GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2, B.coef_f});
-        else
-            force_lane<R, MULTI, ENERGY, TPA, U>(B, L, h, rc2, s, B.nnb + i, l, ti, sw[i], ListGlobal{B.list + i, L.ld},
-                                                 GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2, B.coef_f});
-    }
+    if (active)
+        force_lane<R, MULTI, ENERGY, TPA, U>(B, L, h, rc2, s, B.nnb + i, l, ti, sw[i], ListGlobal{B.list + i, L.ld},
+                                             GlobalFetch<R>{sw}, f, e7, TabGlobal<R>{B.coef2, B.coef_f});
 #pragma unroll
     for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);
     double ke = 0.0;
@@ -507,306 +398,29 @@ __global__ void __launch_bounds__(256) k_force(Bufs<R> B, Geom G, Launch L)
     force_block_end<R, ENERGY>(B, L, e7, ke, lane_sum<TPA>(d2), MODE == MODE_CLOSE_OPEN);
 }
 
-// ---- row-staged schedule (one atom type, fused tables) ----
-
-// Ranges of the 3 x 3 rows around row (cy, cz) and the stage layout; the
-// records are copied in when they fit.  Returns whether the block stages.
-template <class R>
-__device__ __forceinline__ bool stage_rows(const Bufs<R> &B, const Geom &G, const Launch &L, const typename V4<R>::T *sw,
-                                           typename V4<R>::T *stage, int *base, int *rstart, int *rcount, int row)
-{
-    __shared__ int off[10];
-    __shared__ int ok;
-    const int nx = G.ncell[0], ny = G.ncell[1], nz = G.ncell[2];
-    const int cy = row % ny, cz = row / ny;
-    if (threadIdx.x < 9) {
-        const int t = threadIdx.x;
-        int ey = cy + t % 3 - 1, ez = cz + t / 3 - 1;
-        const bool gone = ((ey < 0 || ey >= ny) && ((G.open_mask >> 1) & 1)) ||
-                          ((ez < 0 || ez >= nz) && ((G.open_mask >> 2) & 1));
-        ey += (ey < 0) ? ny : ((ey >= ny) ? -ny : 0);
-        ez += (ez < 0) ? nz : ((ez >= nz) ? -nz : 0);
-        const int r = ez * ny + ey;
-        const int s0 = B.cell_start[r * nx], s1 = B.cell_start[(r + 1) * nx];
-        rstart[t] = s0;
-        rcount[t] = gone ? 0 : s1 - s0;  // no row beyond an open edge
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        off[0] = 0;
-        for (int t = 0; t < 9; ++t) off[t + 1] = off[t] + rcount[t];
-        ok = off[9] <= L.stage_cap;
-        for (int t = 0; t < 9; ++t) base[t] = rstart[t] - off[t];
-    }
-    __syncthreads();
-    if (!ok) return false;
-    for (int t = 0; t < 9; ++t) {
-        const int n0 = rcount[t], s0 = rstart[t], o = off[t];
-        for (int k = threadIdx.x; k < n0; k += blockDim.x) stage[o + k] = sw[s0 + k];
-    }
-    __syncthreads();
-    return true;
-}
-
-template <class R, bool ENERGY, int TPA>
-__global__ void __launch_bounds__(256) k_density_rows(Bufs<R> B, Geom G, Launch L)
-{
-    using R4 = typename V4<R>::T;
-    R4 *stage = reinterpret_cast<R4 *>(dyn);
-    __shared__ int base[9], rstart[9], rcount[9];
-    R h[3];
-    load_h<R>(G, h);
-    const DevState *st = B.st;
-    const int sp = st->sp, s = st->set;
-    R4 *sw = B.shadow[sp];
-    const bool staged = stage_rows<R>(B, G, L, sw, stage, base, rstart, rcount, blockIdx.x);
-    const int a0 = rstart[4], a1 = a0 + rcount[4];  // this row: entry_row 4 is (dy, dz) = (0, 0)
-    const R rc2 = g_rc2<R>(G);
-    const int per = blockDim.x / TPA;
-    const int l = threadIdx.x % TPA;
-    R e_embed = (R)0;
-    for (int c0 = a0; c0 < a1; c0 += per) {
-        const int i = c0 + threadIdx.x / TPA;
-        const bool active = i < a1;
-        R rho = (R)0;
-        if (active) {
-                const ListGlobal list{B.list + i, L.ld};
-            if (staged)
-                rho = density_lane<R, false, TPA, 4>(B, h, rc2, s, B.nnb + i, L.cap, l, stage[i - base[4]], list,
-                                                     StagedFetch<R>{stage, base}, TabGlobal<R>{B.coef2, B.coef_f});
-            else
-                rho = density_lane<R, false, TPA, 4>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], list, GlobalFetch<R>{sw},
-                                                     TabGlobal<R>{B.coef2, B.coef_f});
-        }
-        rho = lane_sum<TPA>(rho);
-        if (active && l == 0) e_embed += embed<R>(B, sw, i, 0, rho);
-    }
-    if (ENERGY) {
-        const R v[1] = {e_embed};
-        block_sums_t<1, R>(v, B.partials, L.pstride, 0);
-    }
-}
-
-template <class R, int MODE, bool ENERGY, int TPA>
-__global__ void __launch_bounds__(256) k_force_rows(Bufs<R> B, Geom G, Launch L)
-{
-    using R4 = typename V4<R>::T;
-    R4 *stage = reinterpret_cast<R4 *>(dyn);
-    __shared__ int base[9], rstart[9], rcount[9];
-    R h[3];
-    load_h<R>(G, h);
-    const DevState *st = B.st;
-    const int sp = st->sp, s = st->set;
-    const R4 *sw = B.shadow[sp];
-    const bool staged = stage_rows<R>(B, G, L, sw, stage, base, rstart, rcount, blockIdx.x);
-    const int a0 = rstart[4], a1 = a0 + rcount[4];
-    const R rc2 = g_rc2<R>(G);
-    const int per = blockDim.x / TPA;
-    const int l = threadIdx.x % TPA;
-    R e7[7] = {0, 0, 0, 0, 0, 0, 0};
-    double ke = 0.0;
-    float d2max = 0.f;
-    for (int c0 = a0; c0 < a1; c0 += per) {
-        const int i = c0 + threadIdx.x / TPA;
-        const bool active = i < a1;
-        R f[3] = {0, 0, 0};
-        if (active) {
-                const ListGlobal list{B.list + i, L.ld};
-            if (staged)
-                force_lane<R, false, ENERGY, TPA, 4>(B, L, h, rc2, s, B.nnb + i, l, 0, stage[i - base[4]], list,
-                                                     StagedFetch<R>{stage, base}, f, e7, TabGlobal<R>{B.coef2, B.coef_f});
-            else
-                force_lane<R, false, ENERGY, TPA, 4>(B, L, h, rc2, s, B.nnb + i, l, 0, sw[i], list, GlobalFetch<R>{sw}, f,
-                                                     e7, TabGlobal<R>{B.coef2, B.coef_f});
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);
-        float d2 = 0.f;
-        if (active) integrate<R, MODE, ENERGY, TPA>(B, L, s, sp, i, l, 0, f, ke, d2);
-        d2max = fmaxf(d2max, lane_sum<TPA>(d2));
-    }
-    force_block_end<R, ENERGY>(B, L, e7, ke, d2max, MODE == MODE_CLOSE_OPEN);
-}
-
-// ---- spline rows in shared memory (FP32, one atom type, fused tables) ----
-//
-// Persistent blocks: each block copies the f rows (density) or the f and phi
-// rows (force) of the fused table into shared memory once, then walks tiles
-// of blockDim / TPA atoms, tile = blockIdx.x, blockIdx.x + gridDim.x, ...;
-// the grid is what fits on the GPU at once, so there is no partial last wave.
-
-__device__ __forceinline__ void copy_rows(const float4 *coef2, int nint, float4 *f_rows, float4 *phi_rows)
-{
-    for (int k = threadIdx.x; k < nint; k += blockDim.x) {
-        f_rows[k] = coef2[2 * k];
-        if (phi_rows) phi_rows[k] = coef2[2 * k + 1];
-    }
-}
-
-template <bool ENERGY, int TPA>
-__global__ void __launch_bounds__(256) k_density_tab(Bufs<float> B, Geom G, Launch L)
-{
-    const DevState *st = B.st;
-    const int sp = st->sp, s = st->set;
-    const int width = blockDim.x / TPA, l = threadIdx.x % TPA;
-    const int ntiles = (L.n + width - 1) / width;
-    // the warp's list columns are asked of L2 one tile ahead; the first
-    // tile's request overlaps the table copy
-    const int wa = (threadIdx.x >> 5) * (32 / TPA), ncol = min(st->max_nnb, L.cap);
-    prefetch_warp_streams<float, false>(B, L, s, blockIdx.x * width + wa, 32 / TPA, ncol);
-    float4 *f_rows = reinterpret_cast<float4 *>(dyn);
-    const int nint = B.tables->fphi.nint;
-    copy_rows(B.coef2, nint, f_rows, nullptr);
-    __syncthreads();
-    float h[3];
-    load_h<float>(G, h);
-    float4 *sw = B.shadow[sp];
-    const float rc2 = g_rc2<float>(G);
-    const TabShared tab{f_rows, nullptr};
-    float e_embed = 0.f;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        if (tile + (int)gridDim.x < ntiles)
-            prefetch_warp_streams<float, false>(B, L, s, (tile + gridDim.x) * width + wa, 32 / TPA, ncol);
-        const int i = tile * width + threadIdx.x / TPA;
-        const bool active = i < L.n;
-        float rho = 0.f;
-        if (active)
-            rho = density_lane<float, false, TPA, PairsInFlight<false>::density>(
-                B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], ListGlobal{B.list + i, L.ld}, GlobalFetch<float>{sw}, tab);
-        rho = lane_sum<TPA>(rho);
-        if (active && l == 0) e_embed += embed<float>(B, sw, i, 0, rho);
-    }
-    if (ENERGY) {
-        const float v[1] = {e_embed};
-        block_sums_t<1, float>(v, B.partials, L.pstride, 0);
-    }
-}
-
-template <int MODE, bool ENERGY, int TPA>
-__global__ void __launch_bounds__(256) k_force_tab(Bufs<float> B, Geom G, Launch L)
-{
-    const DevState *st = B.st;
-    const int sp = st->sp, s = st->set;
-    const int width = blockDim.x / TPA, l = threadIdx.x % TPA;
-    const int ntiles = (L.n + width - 1) / width;
-    const int wa = (threadIdx.x >> 5) * (32 / TPA), ncol = min(st->max_nnb, L.cap);
-    prefetch_warp_streams<float, true>(B, L, s, blockIdx.x * width + wa, 32 / TPA, ncol);
-    const int nint = B.tables->fphi.nint;
-    float4 *f_rows = reinterpret_cast<float4 *>(dyn);
-    float4 *phi_rows = f_rows + nint;
-    copy_rows(B.coef2, nint, f_rows, phi_rows);
-    __syncthreads();
-    float h[3];
-    load_h<float>(G, h);
-    const float4 *sw = B.shadow[sp];
-    const float rc2 = g_rc2<float>(G);
-    const TabShared tab{f_rows, phi_rows};
-    float e7[7] = {0, 0, 0, 0, 0, 0, 0};
-    double ke = 0.0;
-    float d2max = 0.f;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        if (tile + (int)gridDim.x < ntiles)
-            prefetch_warp_streams<float, true>(B, L, s, (tile + gridDim.x) * width + wa, 32 / TPA, ncol);
-        const int i = tile * width + threadIdx.x / TPA;
-        const bool active = i < L.n;
-        float f[3] = {0, 0, 0};
-        if (active)
-            force_lane<float, false, ENERGY, TPA, PairsInFlight<false>::force>(B, L, h, rc2, s, B.nnb + i, l, 0, sw[i],
-                                                     ListGlobal{B.list + i, L.ld}, GlobalFetch<float>{sw}, f, e7, tab);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) f[c] = lane_sum<TPA>(f[c]);
-        float d2 = 0.f;
-        if (active) integrate<float, MODE, ENERGY, TPA>(B, L, s, sp, i, l, 0, f, ke, d2);
-        d2max = fmaxf(d2max, lane_sum<TPA>(d2));
-    }
-    force_block_end<float, ENERGY>(B, L, e7, ke, d2max, MODE == MODE_CLOSE_OPEN);
-}
-
 // ---- dispatch ----
 
 template <class R, bool MULTI, bool ENERGY>
 void density_tpa(const Bufs<R> &B, const Geom &G, const Launch &L)
 {
-    if (!MULTI && L.staged_d) {
-        const size_t sm = (size_t)L.stage_cap * sizeof(typename V4<R>::T);
-        dim3 g(L.nrows), b(L.block_d);
-        switch (L.tpa_d) {
-        case 1: k_density_rows<R, ENERGY, 1><<<g, b, sm, L.stream>>>(B, G, L); break;
-        case 2: k_density_rows<R, ENERGY, 2><<<g, b, sm, L.stream>>>(B, G, L); break;
-        default: k_density_rows<R, ENERGY, 4><<<g, b, sm, L.stream>>>(B, G, L); break;
-        }
-        return;
-    }
-    if constexpr (std::is_same<R, float>::value && !MULTI) {
-        if (L.tab_d) {
-            const size_t sm = table_smem_bytes(L, false);
-            dim3 g(L.nb_d), b(L.block_d);
-            switch (L.tpa_d) {
-            case 1: k_density_tab<ENERGY, 1><<<g, b, sm, L.stream>>>(B, G, L); break;
-            case 2: k_density_tab<ENERGY, 2><<<g, b, sm, L.stream>>>(B, G, L); break;
-            default: k_density_tab<ENERGY, 4><<<g, b, sm, L.stream>>>(B, G, L); break;
-            }
-            return;
-        }
-    }
     dim3 g(L.nb_d), b(L.block_d);
-    if (!MULTI && L.tiled_d && list_tile_bytes(L, L.tpa_d, L.block_d) <= (size_t)kSharedLimitBytes) {
-        const size_t sm = list_tile_bytes(L, L.tpa_d, L.block_d);
-        switch (L.tpa_d) {
-        case 1: k_density<R, MULTI, ENERGY, 1, true><<<g, b, sm, L.stream>>>(B, G, L); break;
-        case 2: k_density<R, MULTI, ENERGY, 2, true><<<g, b, sm, L.stream>>>(B, G, L); break;
-        default: k_density<R, MULTI, ENERGY, 4, true><<<g, b, sm, L.stream>>>(B, G, L); break;
-        }
-        return;
-    }
     switch (L.tpa_d) {
-    case 1: k_density<R, MULTI, ENERGY, 1, false><<<g, b, 0, L.stream>>>(B, G, L); break;
-    case 2: k_density<R, MULTI, ENERGY, 2, false><<<g, b, 0, L.stream>>>(B, G, L); break;
-    case 4: k_density<R, MULTI, ENERGY, 4, false><<<g, b, 0, L.stream>>>(B, G, L); break;
-    default: k_density<R, MULTI, ENERGY, 8, false><<<g, b, 0, L.stream>>>(B, G, L); break;
+    case 1: k_density<R, MULTI, ENERGY, 1><<<g, b, 0, L.stream>>>(B, G, L); break;
+    case 2: k_density<R, MULTI, ENERGY, 2><<<g, b, 0, L.stream>>>(B, G, L); break;
+    case 4: k_density<R, MULTI, ENERGY, 4><<<g, b, 0, L.stream>>>(B, G, L); break;
+    default: k_density<R, MULTI, ENERGY, 8><<<g, b, 0, L.stream>>>(B, G, L); break;
     }
 }
 
 template <class R, bool MULTI, int MODE, bool ENERGY>
 void force_tpa(const Bufs<R> &B, const Geom &G, const Launch &L)
 {
-    if (!MULTI && L.staged_f) {
-        const size_t sm = (size_t)L.stage_cap * sizeof(typename V4<R>::T);
-        dim3 g(L.nrows), b(L.block_f);
-        switch (L.tpa_f) {
-        case 1: k_force_rows<R, MODE, ENERGY, 1><<<g, b, sm, L.stream>>>(B, G, L); break;
-        case 2: k_force_rows<R, MODE, ENERGY, 2><<<g, b, sm, L.stream>>>(B, G, L); break;
-        default: k_force_rows<R, MODE, ENERGY, 4><<<g, b, sm, L.stream>>>(B, G, L); break;
-        }
-        return;
-    }
-    if constexpr (std::is_same<R, float>::value && !MULTI) {
-        if (L.tab_f) {
-            const size_t sm = table_smem_bytes(L, true);
-            dim3 g(L.nb_f), b(L.block_f);
-            switch (L.tpa_f) {
-            case 1: k_force_tab<MODE, ENERGY, 1><<<g, b, sm, L.stream>>>(B, G, L); break;
-            case 2: k_force_tab<MODE, ENERGY, 2><<<g, b, sm, L.stream>>>(B, G, L); break;
-            default: k_force_tab<MODE, ENERGY, 4><<<g, b, sm, L.stream>>>(B, G, L); break;
-            }
-            return;
-        }
-    }
     dim3 g(L.nb_f), b(L.block_f);
-    if (!MULTI && L.tiled_f && list_tile_bytes(L, L.tpa_f, L.block_f) <= (size_t)kSharedLimitBytes) {
-        const size_t sm = list_tile_bytes(L, L.tpa_f, L.block_f);
-        switch (L.tpa_f) {
-        case 1: k_force<R, MULTI, MODE, ENERGY, 1, true><<<g, b, sm, L.stream>>>(B, G, L); break;
-        case 2: k_force<R, MULTI, MODE, ENERGY, 2, true><<<g, b, sm, L.stream>>>(B, G, L); break;
-        default: k_force<R, MULTI, MODE, ENERGY, 4, true><<<g, b, sm, L.stream>>>(B, G, L); break;
-        }
-        return;
-    }
     switch (L.tpa_f) {
-    case 1: k_force<R, MULTI, MODE, ENERGY, 1, false><<<g, b, 0, L.stream>>>(B, G, L); break;
-    case 2: k_force<R, MULTI, MODE, ENERGY, 2, false><<<g, b, 0, L.stream>>>(B, G, L); break;
-    case 4: k_force<R, MULTI, MODE, ENERGY, 4, false><<<g, b, 0, L.stream>>>(B, G, L); break;
-    default: k_force<R, MULTI, MODE, ENERGY, 8, false><<<g, b, 0, L.stream>>>(B, G, L); break;
+    case 1: k_force<R, MULTI, MODE, ENERGY, 1><<<g, b, 0, L.stream>>>(B, G, L); break;
+    case 2: k_force<R, MULTI, MODE, ENERGY, 2><<<g, b, 0, L.stream>>>(B, G, L); break;
+    case 4: k_force<R, MULTI, MODE, ENERGY, 4><<<g, b, 0, L.stream>>>(B, G, L); break;
+    default: k_force<R, MULTI, MODE, ENERGY, 8><<<g, b, 0, L.stream>>>(B, G, L); break;
     }
 }
 
@@ -823,66 +437,6 @@ void force_modes(const Bufs<R> &B, const Geom &G, const Launch &L, int mode, boo
         if (energy) force_tpa<R, MULTI, MODE_CLOSE_OPEN, true>(B, G, L);
         else force_tpa<R, MULTI, MODE_CLOSE_OPEN, false>(B, G, L);
     }
-}
-
-// Shared-memory opt-in of the row-staged kernels for `bytes` of stage.
-template <class K>
-cudaError_t allow_bytes(K kernel, int bytes)
-{
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
-
-template <class R, int MODE, bool ENERGY>
-cudaError_t allow_tiled_force(int bytes)
-{
-    cudaError_t e = allow_bytes(k_force<R, false, MODE, ENERGY, 1, true>, bytes);
-    if (e == cudaSuccess) e = allow_bytes(k_force<R, false, MODE, ENERGY, 2, true>, bytes);
-    if (e == cudaSuccess) e = allow_bytes(k_force<R, false, MODE, ENERGY, 4, true>, bytes);
-    return e;
-}
-
-template <class R, bool ENERGY>
-cudaError_t allow_tiled_density(int bytes)
-{
-    cudaError_t e = allow_bytes(k_density<R, false, ENERGY, 1, true>, bytes);
-    if (e == cudaSuccess) e = allow_bytes(k_density<R, false, ENERGY, 2, true>, bytes);
-    if (e == cudaSuccess) e = allow_bytes(k_density<R, false, ENERGY, 4, true>, bytes);
-    return e;
-}
-
-template <int MODE>
-cudaError_t allow_tab_force(int bytes)
-{
-    cudaError_t e = cudaSuccess;
-    for (int t : {1, 2, 4}) {
-        if (e != cudaSuccess) break;
-        e = allow_bytes(t == 1 ? k_force_tab<MODE, false, 1> : (t == 2 ? k_force_tab<MODE, false, 2> : k_force_tab<MODE, false, 4>), bytes);
-        if (e == cudaSuccess)
-            e = allow_bytes(t == 1 ? k_force_tab<MODE, true, 1> : (t == 2 ? k_force_tab<MODE, true, 2> : k_force_tab<MODE, true, 4>), bytes);
-    }
-    return e;
-}
-
-template <class R, int MODE, bool ENERGY>
-cudaError_t allow_rows_force(int bytes)
-{
-    cudaError_t e = cudaFuncSetAttribute(k_force_rows<R, MODE, ENERGY, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_force_rows<R, MODE, ENERGY, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_force_rows<R, MODE, ENERGY, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return e;
-}
-
-template <class R, bool ENERGY>
-cudaError_t allow_rows_density(int bytes)
-{
-    cudaError_t e = cudaFuncSetAttribute(k_density_rows<R, ENERGY, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_density_rows<R, ENERGY, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_density_rows<R, ENERGY, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return e;
 }
 
 }  // namespace
@@ -906,57 +460,6 @@ int launch_force(const Bufs<R> &B, const Geom &G, const Launch &L, int mode, boo
     if (L.multi) force_modes<R, true>(B, G, L, mode, energy);
     else force_modes<R, false>(B, G, L, mode, energy);
     return 1;
-}
-
-// Resident blocks per SM of the shared-table passes (the hot force variant).
-inline int table_blocks_per_sm(const Launch &L, bool force, int tpa, int block)
-{
-    int nb = 0;
-    const size_t sm = table_smem_bytes(L, force);
-    cudaError_t e;
-    if (force)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &nb, tpa == 1 ? k_force_tab<MODE_CLOSE_OPEN, false, 1>
-                          : (tpa == 2 ? k_force_tab<MODE_CLOSE_OPEN, false, 2> : k_force_tab<MODE_CLOSE_OPEN, false, 4>),
-            block, sm);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &nb, tpa == 1 ? k_density_tab<false, 1> : (tpa == 2 ? k_density_tab<false, 2> : k_density_tab<false, 4>),
-            block, sm);
-    return e == cudaSuccess ? nb : 0;
-}
-
-template <class R>
-cudaError_t allow_shared_staging(int bytes)
-{
-    cudaError_t e = allow_rows_density<R, false>(bytes);
-    if (e == cudaSuccess) e = allow_rows_density<R, true>(bytes);
-    if (e == cudaSuccess) e = allow_rows_force<R, MODE_MEASURE, false>(bytes);
-    if (e == cudaSuccess) e = allow_rows_force<R, MODE_MEASURE, true>(bytes);
-    if (e == cudaSuccess) e = allow_rows_force<R, MODE_CLOSE, false>(bytes);
-    if (e == cudaSuccess) e = allow_rows_force<R, MODE_CLOSE, true>(bytes);
-    if (e == cudaSuccess) e = allow_rows_force<R, MODE_CLOSE_OPEN, false>(bytes);
-    if (e == cudaSuccess) e = allow_rows_force<R, MODE_CLOSE_OPEN, true>(bytes);
-    if (e == cudaSuccess) e = allow_tiled_density<R, false>(bytes);
-    if (e == cudaSuccess) e = allow_tiled_density<R, true>(bytes);
-    if (e == cudaSuccess) e = allow_tiled_force<R, MODE_MEASURE, false>(bytes);
-    if (e == cudaSuccess) e = allow_tiled_force<R, MODE_MEASURE, true>(bytes);
-    if (e == cudaSuccess) e = allow_tiled_force<R, MODE_CLOSE, false>(bytes);
-    if (e == cudaSuccess) e = allow_tiled_force<R, MODE_CLOSE, true>(bytes);
-    if (e == cudaSuccess) e = allow_tiled_force<R, MODE_CLOSE_OPEN, false>(bytes);
-    if (e == cudaSuccess) e = allow_tiled_force<R, MODE_CLOSE_OPEN, true>(bytes);
-    if constexpr (std::is_same<R, float>::value) {
-        for (int t : {1, 2, 4}) {
-            if (e != cudaSuccess) break;
-            e = allow_bytes(t == 1 ? k_density_tab<false, 1> : (t == 2 ? k_density_tab<false, 2> : k_density_tab<false, 4>), bytes);
-            if (e == cudaSuccess)
-                e = allow_bytes(t == 1 ? k_density_tab<true, 1> : (t == 2 ? k_density_tab<true, 2> : k_density_tab<true, 4>), bytes);
-        }
-        if (e == cudaSuccess) e = allow_tab_force<MODE_MEASURE>(bytes);
-        if (e == cudaSuccess) e = allow_tab_force<MODE_CLOSE>(bytes);
-        if (e == cudaSuccess) e = allow_tab_force<MODE_CLOSE_OPEN>(bytes);
-    }
-    return e;
 }
 
 

@@ -69,8 +69,7 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu():
 
 
 @pytest.mark.parametrize("kw", [dict(lanes_per_atom=3), dict(block_size=100), dict(block_size=512),
-                                dict(schedule="rows", lanes_per_atom=8), dict(schedule="table", lanes_per_atom=8),
-                                dict(stage_capacity=-1)])
+                                dict(wait_limit_us=-1)])
 def test_create_rejects_bad_options_before_touching_the_gpu(kw):
     from paper_2405_07898_gb300 import inputs as I
     s = I.bcc_2000_fp64()
@@ -80,7 +79,7 @@ def test_create_rejects_bad_options_before_touching_the_gpu(kw):
 
 
 def test_create_rejects_out_of_range_enums():
-    """schedule and persistent outside their enumerations (set in the raw
+    """persistent and precision outside their enumerations (set in the raw
     options struct, past what the Python names allow)."""
     from paper_2405_07898_gb300 import inputs as I
     s = I.bcc_2000_fp64()
@@ -93,7 +92,7 @@ def test_create_rejects_out_of_range_enums():
     pos = np.ascontiguousarray(s.pos, dtype=np.float64)
     types = np.ascontiguousarray(s.types, dtype=np.int32)
     dp = ctypes.POINTER(ctypes.c_double)
-    for field, value in (("schedule", 5), ("persistent", 4), ("precision", 2)):
+    for field, value in (("persistent", 3), ("persistent", -1), ("precision", 2)):
         opt = binding.Options()
         lib.md_options_default(ctypes.byref(opt))
         setattr(opt, field, value)

@@ -4,7 +4,7 @@ free-surface slabs of the paper's benchmark systems.
 Bars as for periodic systems: cell bins and neighbour lists bit-exact (same
 order), FP64 forces within 1e-10 and mixed-precision forces within 2e-5 of
 the oracle (relative 2-norm over all 3N components), trajectories within
-1e-9 A in FP64; every schedule and the single launch bitwise equal to the
+1e-9 A in FP64; the single launch bitwise equal to the
 atom-parallel graph path.
 """
 import numpy as np
@@ -94,26 +94,20 @@ def test_open_trajectory_fp64_matches_oracle():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_open_schedules_and_single_launch_bitwise(precision):
-    """Row staging must drop rows beyond open y/z edges; tiles, the shared
-    table and both forms of the single launch follow the same lists."""
+def test_open_single_launch_bitwise(precision):
+    """The single launch follows the same lists across open edges as the
+    graph path: forces and positions bitwise equal after 30 steps."""
     s = I.bcc_slab_small(7)
     out = {}
-    for name, kw in (("atoms", dict(schedule="atoms", persistent="off")),
-                     ("rows", dict(schedule="rows", persistent="off")),
-                     ("tiles", dict(schedule="tiles", persistent="off")),
-                     ("table", dict(schedule="table", persistent="off")),
-                     ("single", dict(schedule="atoms", persistent="on")),
-                     ("cluster", dict(schedule="atoms", persistent="cluster"))):
+    for name, kw in (("graphs", dict(persistent="off")), ("single", dict(persistent="on"))):
         with binding.MD(s, precision=precision, lanes_per_atom=2, **kw) as md:
             f0 = md.forces()
             md.step(30, 2.0)
             out[name] = (f0, md.get_state()[0], md.forces())
-    for name in ("rows", "tiles", "table", "single", "cluster"):
-        for a, b in zip(out[name], out["atoms"]):
-            np.testing.assert_array_equal(a, b)
-    _, _, F, _, _ = oracle_eval(s, out["atoms"][1])
-    assert_forces(out["atoms"][2], F, precision)
+    for a, b in zip(out["single"], out["graphs"]):
+        np.testing.assert_array_equal(a, b)
+    _, _, F, _, _ = oracle_eval(s, out["graphs"][1])
+    assert_forces(out["graphs"][2], F, precision)
 
 
 def test_paper_size_ta_slab_forces():

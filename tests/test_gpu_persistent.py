@@ -120,15 +120,12 @@ def test_single_launch_after_set_state_and_auto_threshold():
         assert md.stats()["persistent_blocks"] == 0
 
 
-@pytest.mark.parametrize("form", ["on", "cluster"])
-def test_wait_limit_raises_timeout_and_the_context_recovers(form):
+def test_wait_limit_raises_timeout_and_the_context_recovers():
     """A barrier wait longer than the configured limit (1 us here, so the
     barriers of the single launch run out) ends the launch with
-    MD_ERR_TIMEOUT; md_set_state clears it and the context answers again.
-    In the cluster form a CTA that gave up stays until every CTA has left or
-    given up (the others may still read its shared memory)."""
+    MD_ERR_TIMEOUT; md_set_state clears it and the context answers again."""
     s = I.bcc_2000_fp64()
-    with binding.MD(s, precision="mixed", persistent=form, lanes_per_atom=2, schedule="atoms", wait_limit_us=1) as md:
+    with binding.MD(s, precision="mixed", persistent="on", lanes_per_atom=2, wait_limit_us=1) as md:
         md.step(200, 2.0)
         with pytest.raises(binding.MDError) as e:
             md.sync()
@@ -138,91 +135,3 @@ def test_wait_limit_raises_timeout_and_the_context_recovers(form):
     with pytest.raises(binding.MDError) as e:
         binding.MD(s, wait_limit_us=-1)
     assert e.value.status == -1
-
-
-# ---- the cluster form: one thread-block cluster, records in shared memory ----
-
-def run_cluster_pair(system, precision, lanes, calls, dt, schedule="atoms", **kw):
-    """The same md_step calls on a cluster-form single launch and a graph
-    context with the same lanes per atom."""
-    out = []
-    for persistent in ("cluster", "off"):
-        with binding.MD(system, precision=precision, lanes_per_atom=lanes, persistent=persistent,
-                        schedule=schedule if persistent == "cluster" else "atoms", **kw) as md:
-            st = md.stats()
-            if persistent == "cluster":
-                assert st["persistent_cluster"] == (2 if schedule == "table" else 1)
-                assert 1 <= st["persistent_blocks"] <= 16
-                assert st["persistent_lanes"] == lanes
-            else:
-                assert st["persistent_cluster"] == 0 and st["persistent_blocks"] == 0
-            for nsteps in calls:
-                md.step(nsteps, dt)
-            pos, vel, step = md.get_state()
-            out.append(dict(pos=pos, vel=vel, step=step, forces=md.forces(), energy=md.energy(),
-                            virial=md.virial(), stats=md.stats()))
-    return out
-
-
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("lanes", [1, 2, 8])
-def test_cluster_launch_equals_graphs(precision, lanes):
-    """2,000 atoms: 8 CTAs of 256 atoms (1 lane), 16 of 128 (2 lanes; the
-    last CTA holds 80), 16 of 128 walked as 4 tiles of 32 (8 lanes)."""
-    s = I.bcc_2000_fp64()
-    a, b = run_cluster_pair(s, precision, lanes, [37, 1, 12], 2.0)
-    assert a["stats"]["persistent_blocks"] == {1: 8, 2: 16, 8: 16}[lanes]
-    np.testing.assert_array_equal(a["pos"], b["pos"])
-    np.testing.assert_array_equal(a["vel"], b["vel"])
-    np.testing.assert_array_equal(a["forces"], b["forces"])
-    assert a["step"] == b["step"] == 50
-    assert a["stats"]["rebuilds"] == b["stats"]["rebuilds"] >= 4
-    for x, y in zip(a["energy"], b["energy"]):
-        assert abs(x - y) <= ETOL[precision] * abs(y)
-    # a CTA walks several tiles, so the per-lane FP32 sums take other terms:
-    # rounding relative to the tensor's scale (off-diagonals are cancellations)
-    np.testing.assert_allclose(a["virial"], b["virial"], rtol=0,
-                               atol=ETOL[precision] * 100 * np.abs(b["virial"]).max())
-    assert_forces(a["forces"], oracle_forces(s, a["pos"]), precision)
-
-
-@pytest.mark.parametrize("lanes", [1, 4])
-def test_cluster_launch_shared_tables_equal_graphs(lanes):
-    """FP32 with the fused spline rows copied into every CTA's shared memory."""
-    s = I.bcc_2000_fp64()
-    a, b = run_cluster_pair(s, "mixed", lanes, [23, 7], 2.0, schedule="table")
-    np.testing.assert_array_equal(a["pos"], b["pos"])
-    np.testing.assert_array_equal(a["vel"], b["vel"])
-    np.testing.assert_array_equal(a["forces"], b["forces"])
-
-
-def test_cluster_launch_displacement_rebuilds_and_two_types():
-    """Builds triggered by displacement are decided from the maxima the CTAs
-    exchange with their barrier arrivals; the type-dependent path too."""
-    s = I.thermal_system(I.BCC_TA_LIKE, (10, 10, 10), 0.02, 3000.0, 99)
-    a, b = run_cluster_pair(s, "fp64", 2, [60], 4.0, rebuild_every=1000)
-    np.testing.assert_array_equal(a["pos"], b["pos"])
-    assert a["stats"]["rebuilds"] == b["stats"]["rebuilds"] > 0
-    m = I.multi_type_system()
-    a, b = run_cluster_pair(m, "mixed", 4, [25], 2.0)
-    np.testing.assert_array_equal(a["pos"], b["pos"])
-    np.testing.assert_array_equal(a["forces"], b["forces"])
-
-
-def test_cluster_launch_sizes_and_limits():
-    """Small and ragged systems: 250 atoms in one CTA, 432 in 7 CTAs of 64
-    (the last holds 48), 1,024 in 16 CTAs of 64 at 4 lanes; a system whose
-    state does not fit the shared memory of 16 CTAs is refused."""
-    for cells, lanes, ncta in ((5, 1, 1), (6, 4, 7), (8, 4, 16)):
-        s = I.bcc_cube(cells)
-        a, b = run_cluster_pair(s, "mixed", lanes, [15], 2.0)
-        assert a["stats"]["persistent_blocks"] == ncta
-        np.testing.assert_array_equal(a["pos"], b["pos"])
-        np.testing.assert_array_equal(a["forces"], b["forces"])
-    big = I.bcc_cube(26)  # 35,152 atoms
-    with pytest.raises(binding.MDError) as e:
-        binding.MD(big, precision="mixed", persistent="cluster")
-    assert e.value.status == -3  # MD_ERR_CUDA
-    with binding.MD(I.bcc_cube(8), precision="mixed") as md:  # automatic: one of the two forms
-        st = md.stats()
-        assert st["persistent_blocks"] > 0 and st["persistent_cluster"] in (0, 1, 2)
