@@ -1126,14 +1126,14 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     L.block = o.block_size;
     L.nblocks = (int)((n + L.block - 1) / L.block);
     {
-        // the list build (one warp per cell) of a small system: as few cells
-        // per block as it takes to give every SM two blocks (down to one)
+        // the list build of a small system: blocks as small as it takes to
+        // give every SM two (down to one warp)
         int dev = 0, nsm = 152;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             nsm = 152;
-        int wpb = kListWarps;
-        while (wpb > 1 && ((int64_t)G.ncells + wpb - 1) / wpb < 2 * (int64_t)nsm) wpb /= 2;
-        L.list_block = 32 * wpb;
+        L.list_block = L.block;
+        while (L.list_block > 32 && (n + L.list_block - 1) / L.list_block < 2 * (int64_t)nsm) L.list_block /= 2;
+        L.list_block = std::max(32, L.list_block / 32 * 32);
     }
     L.pstride = std::max(1, blocks_for_host(8 * n, std::min(L.block, 128)));
     {

@@ -39,7 +39,6 @@ __host__ __device__ constexpr uint32_t list_entry(uint32_t q, int dx, int dy, in
     return q | ((uint32_t)((dx + 1) | ((dy + 1) << 2) | ((dz + 1) << 4)) << kCodeShift);
 }
 constexpr int kScanBlock = 1024;
-constexpr int kListWarps = 8;  // most cells (warps) per block of the list build
 constexpr int kEnergySlots = 10;  // embed, pair, ke, virial xx yy zz xy xz yz, spare
 constexpr double kAccel = 9.648533215665e-3;  // (eV/Angstrom/amu) -> Angstrom/fs^2
 
@@ -144,7 +143,7 @@ struct Launch {
     int ld;         // list leading dimension (multiple of 32)
     int cap;        // list slots per atom
     int block;      // threads per block of per-atom kernels
-    int list_block; // threads per block of the list build: one warp per cell, fewer cells per block for small systems
+    int list_block; // threads per block of the list build (smaller for small systems, to fill the SMs)
     int block_d;    // threads per block of the density pass
     int block_f;    // threads per block of the force pass
     int nblocks;    // ceil(n / block)
