@@ -17,6 +17,12 @@ MD timesteps per second (higher is better).
           md_set_state from pinned host memory (positions + velocities),
           md_step(10), md_energy (reads PE and KE back)
 
+After the timed region (rank 0, one GPU) the line also carries short legs
+measured in the same run: the plain FP64 GPU path on the same system
+(`fp64`, and the mixed/FP64 ratio), the half-list form (`half_list`), the
+512-replica batched launch (`batch`, atom-steps/s) and the oracle on all host
+cores (`cpu_baseline_all_cores`); --no-extras leaves them out.
+
 --impl reference times the CPU oracle (the plain serial FP64 C reference)
 on a bounded sample of the same workload: one timestep per benchmark step.
 With torchrun (N > 1) every rank advances its own replica of the system
@@ -74,7 +80,7 @@ class ClockSampler:
         try:
             self._proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "10"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self._proc = None
             return
@@ -103,7 +109,8 @@ class ClockSampler:
             self._proc.kill()
         if self._thread:
             self._thread.join(timeout=2)
-        rows = self.rows[getattr(self, "_mark", 0):] or self.rows
+        marked = self.rows[getattr(self, "_mark", 0):]
+        rows = marked or self.rows
         sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -114,7 +121,8 @@ class ClockSampler:
                     if r[5 + k].lower() == "active":
                         reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "interval_ms": 10,
+                "samples_are": "timed region" if marked else "warm-up and timed region (none inside the timed region)"}
 
 
 def algorithmic_bytes(n_half: int):
@@ -148,7 +156,8 @@ def run_ours(args):
     else:
         system = I.bcc_799496()
     n = system.n
-    md = binding.MD(system, precision=args.precision, rebuild_every=10, use_graphs=not args.eager)
+    md = binding.MD(system, precision=args.precision, rebuild_every=10, use_graphs=not args.eager,
+                    half_list=args.half_list)
     stream = md.stream
 
     def bench_step():
@@ -212,6 +221,9 @@ def run_ours(args):
     e2e_value = world * args.e2e_steps * MD_STEPS_PER_BENCH_STEP / e2e_s
     md.close()
 
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras and not args.cells:
+        extras = extra_legs(args, system, ts_per_s)
     if rank == 0:
         cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu_baseline) else None
         line = {
@@ -230,7 +242,8 @@ def run_ours(args):
             "config": {"workload": (WORKLOAD if not args.cells else system.label + "_mixed").replace(
                            "_mixed", "_" + args.precision), "atoms": n, "md_steps_per_step": MD_STEPS_PER_BENCH_STEP,
                        "dt_fs": DT_FS, "rebuild_every": 10, "precision": args.precision,
-                       "list": "full Verlet list, r_list 4.8 A, 26 entries/atom",
+                       "list": ("half Verlet list (each pair once), r_list 4.8 A, 13 entries/atom" if args.half_list
+                                else "full Verlet list, r_list 4.8 A, 26 entries/atom"),
                        "l2": "working set ~0.35 GB > L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "launch": "eager" if args.eager else "cuda graphs",
@@ -253,9 +266,64 @@ def run_ours(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def extra_legs(args, system, mixed_ts_per_s):
+    """Short measurements beside the headline, in the same run: the plain
+    FP64 GPU path and the half-list form on the same 799,496-atom system
+    (device time of whole bench steps, CUDA events on the library's stream),
+    the 512-replica batched launch, and the oracle on all host cores."""
+    import torch
+    from paper_2405_07898_gb300 import binding, inputs as I
+
+    out = {}
+    # FP64 GPU path: the comparison the mixed form is held to (>= 1.5x)
+    with binding.MD(system, precision="fp64", rebuild_every=10) as md:
+        md.step(MD_STEPS_PER_BENCH_STEP, DT_FS)
+        k = 3
+        t = _timed_steps(md, MD_STEPS_PER_BENCH_STEP, DT_FS, reps=k)
+        v = k * MD_STEPS_PER_BENCH_STEP / t
+    out["fp64"] = {"value": v, "unit": "timesteps/s", "bench_steps": k,
+                   "mixed_over_fp64": mixed_ts_per_s / v,
+                   "note": "plain FP64 GPU path (all pair, density and force arithmetic in FP64), same system"}
+    # half lists: each pair once, the other end's terms through fixed-point sums
+    with binding.MD(system, precision="mixed", rebuild_every=10, half_list=True) as md:
+        for _ in range(3):
+            md.step(MD_STEPS_PER_BENCH_STEP, DT_FS)
+        k = 30
+        t = _timed_steps(md, MD_STEPS_PER_BENCH_STEP, DT_FS, reps=k)
+        prof = md.profile(args.profile_steps, DT_FS)
+        st = md.stats()
+    out["half_list"] = {"value": k * MD_STEPS_PER_BENCH_STEP / t, "unit": "timesteps/s", "bench_steps": k,
+                        "max_neighbors": st["max_neighbors"],
+                        "kernels_ms": {"density": prof["density_ms"], "force": prof["force_ms"],
+                                       "rebuild": prof["rebuild_ms"], "step": prof["step_ms"]},
+                        "note": "density = pair pass + F' pass; force = pair pass + integration pass"}
+    # the batched form: 512 replicas of uneven size in one persistent launch
+    reps = I.replica_batch(512)
+    with binding.MDBatch(reps) as b:
+        b.step(10, DT_FS)
+        b.energy()
+        info = b.info()
+        nsteps = args.batch_steps_extra
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(b.stream)
+        b.step(nsteps, DT_FS)
+        e1.record(b.stream)
+        b.energy()
+        ms = e0.elapsed_time(e1)
+    out["batch"] = {"value": info["atoms"] * nsteps / (ms * 1e-3), "unit": "atom-steps/s",
+                    "workload": "replicas_512_bcc_fcc_mixed", "replicas": info["replicas"], "atoms": info["atoms"],
+                    "steps": nsteps, "ms": ms, "threads_per_block": info["threads_per_block"]}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args)
+    return out
 
 
 def _timed_steps(md, nsteps, dt, reps=1):
@@ -554,6 +622,25 @@ def _oracle_sample(nsteps: int):
     return dt, s.n
 
 
+def cpu_baseline_all_cores(args):
+    """The oracle's OpenMP build (its per-atom loops in parallel; the list
+    build serial) on every host core, over the same bounded sample."""
+    import oracle as O
+    from paper_2405_07898_gb300 import inputs as I
+
+    s = I.bcc_799496()
+    pot = O.Potential(s.pot, L=O.lib_omp())
+    sysm = O.System(pot, s.box, s.pos, s.vel, s.types)
+    steps = args.cpu_steps
+    t0 = time.perf_counter()
+    sysm.step(steps, DT_FS)
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count()
+    return {"value": steps / dt, "unit": "timesteps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} timesteps of the 799,496-atom system (the oracle's OpenMP build on {cores} "
+                      f"threads; list build serial), {dt:.1f} s"}
+
+
 def cpu_baseline(args):
     steps = args.cpu_steps
     dt, n = _oracle_sample(steps)
@@ -614,6 +701,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave out the FP64, half-list, batch and all-cores legs of the default line")
+    ap.add_argument("--batch-steps-extra", type=int, default=200,
+                    help="steps of the batch leg in the default line")
+    ap.add_argument("--half-list", action="store_true",
+                    help="run the timed workload in the half-list form (profiling)")
     ap.add_argument("--workload", default="bcc_799496", choices=["bcc_799496", "sweep", "drift", "batch", "adjoint", "model", "slab"],
                     help="bcc_799496: the benchmark line; sweep / drift: the strong-scaling sweep and the "
                          "NVE drift runs (their own JSON lines)")

@@ -141,7 +141,24 @@ enum { MD_PERSIST_AUTO = 0, MD_PERSIST_OFF = 1, MD_PERSIST_ON = 2 };
  *   batch_schedule   batches only: 0 = threads per block and resident
  *                    blocks per SM timed at md_batch_create (unless
  *                    lanes_per_atom > 0, which takes 512 x 1); 1..5 =
- *                    512 x 1, 256 x 2, 256 x 3, 1024 x 1, 512 x 2. */
+ *                    512 x 1, 256 x 2, 256 x 3, 1024 x 1, 512 x 2.
+ *   half_list        0: every atom lists all its neighbours and each pair is
+ *                    evaluated from both ends (the default).  1: the
+ *                    force-symmetry form (Section "Future Work"): each pair
+ *                    is listed once -- by the atom that sees the other in
+ *                    the upper half space (pair vector with d_z > 0, ties
+ *                    broken by d_y, then d_x, decided exactly) -- and
+ *                    evaluated once; the term for the other atom is added
+ *                    to it through per-atom 64-bit fixed-point accumulators
+ *                    (2^-32 units of density or eV/Angstrom) by integer
+ *                    atomics, whose totals do not depend on arrival order,
+ *                    so runs are bitwise reproducible.  Mixed precision with
+ *                    one atom type whose f and phi share a knot grid only
+ *                    (MD_ERR_ARG otherwise); md_step runs as CUDA graphs
+ *                    (or eagerly), never as the single launch; lanes per
+ *                    atom are 1.  A pair term beyond 2^24 in magnitude (out
+ *                    of the accumulators' range) raises MD_ERR_NONFINITE.
+ *                    md_neighbors still reports every atom's full list. */
 typedef struct {
     int32_t precision;
     int32_t rebuild_every;
@@ -157,6 +174,7 @@ typedef struct {
     int32_t wait_limit_us;
     int32_t open_axes;
     int32_t batch_schedule;
+    int32_t half_list;
 } md_options;
 
 void md_options_default(md_options *opt);
@@ -230,6 +248,8 @@ typedef struct {
     int32_t threads_force;   /* threads per block of the force pass */
     int32_t persistent_blocks; /* blocks of the single-launch md_step (0: graphs) */
     int32_t persistent_lanes;  /* lanes per atom of its pair passes */
+    int32_t half_list;         /* 1: pairs listed and evaluated once (md_options.half_list) */
+    int32_t reserved;
 } md_stats_t;
 
 md_status md_stats(md_ctx *ctx, md_stats_t *out);

@@ -21,22 +21,35 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "eam_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
 _lp = C.POINTER(C.c_int64)
 
 
+def _compile(out: str, extra, force: bool) -> str:
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", *extra, "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction: every operation is
-    rounded as written)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    rounded as written; one thread).  This is the build every parity test
+    uses."""
+    return _compile(_LIB, [], force)
+
+
+def build_omp(force: bool = False) -> str:
+    """The same source built with OpenMP, used only to time the oracle on all
+    host cores (its per-atom loops run in parallel; sums over atoms are taken
+    in another order, so its energies may differ from build() in rounding)."""
+    return _compile(_LIB_OMP, ["-fopenmp"], force)
 
 
 class _Knots(C.Structure):
@@ -46,48 +59,62 @@ class _Knots(C.Structure):
 
 
 _lib = None
+_lib_omp = None
 
 
 def lib():
+    """The parity build (one thread)."""
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
-        L.orc_spline_coeffs.argtypes = [C.c_int32, C.c_double, _dp, C.c_int32, C.c_double,
-                                        C.c_int32, C.c_double, _dp]
-        L.orc_spline_coeffs.restype = C.c_int
-        L.orc_spline_eval.argtypes = [C.c_int32, C.c_double, C.c_double, _dp, C.c_double, _dp, _dp]
-        L.orc_spline_eval.restype = C.c_double
-        L.orc_pot_create.argtypes = [C.c_int32, _dp, C.POINTER(_Knots), C.POINTER(_Knots),
-                                     C.POINTER(_Knots), C.c_double, C.c_double]
-        L.orc_pot_create.restype = C.c_void_p
-        L.orc_pot_destroy.argtypes = [C.c_void_p]
-        L.orc_wrap.argtypes = [C.c_int64, _dp, C.c_int, _dp]
-        L.orc_cell_dims.argtypes = [_dp, C.c_int, C.c_double, _ip]
-        L.orc_cell_dims.restype = C.c_int
-        L.orc_cells.argtypes = [C.c_int64, _dp, C.c_int, C.c_double, _dp, _ip, _ip]
-        L.orc_cells.restype = C.c_int
-        for name in ("orc_list_cells", "orc_list_brute"):
-            fn = getattr(L, name)
-            fn.argtypes = [C.c_int64, _dp, C.c_int, C.c_double, _dp, _lp, _ip, C.c_int64]
-            fn.restype = C.c_int64
-        L.orc_eam_eval.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int, _dp, _ip, _lp, _ip, _dp, _dp, _dp,
-                                   _dp, _dp]
-        L.orc_eam_eval.restype = C.c_int
-        L.orc_sys_create.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int, _dp, _dp, _ip]
-        L.orc_sys_create.restype = C.c_void_p
-        L.orc_sys_destroy.argtypes = [C.c_void_p]
-        L.orc_sys_step.argtypes = [C.c_void_p, C.c_int64, C.c_double, C.c_int32]
-        L.orc_sys_step.restype = C.c_int
-        L.orc_sys_energy.argtypes = [C.c_void_p, _dp, _dp]
-        L.orc_sys_virial.argtypes = [C.c_void_p, _dp]
-        L.orc_sys_get.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, _dp, _lp]
-        L.orc_spline_basis.argtypes = [C.c_int32, C.c_double, C.c_int32, C.c_int32, _dp]
-        L.orc_spline_basis.restype = C.c_int
-        L.orc_force_match.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int, _dp, C.c_double, _dp, C.c_double,
-                                      _dp, _dp, _dp, _dp, _dp, _dp]
-        L.orc_force_match.restype = C.c_int
-        _lib = L
+        _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+def lib_omp():
+    """The all-cores timing build (see build_omp)."""
+    global _lib_omp
+    if _lib_omp is None:
+        _lib_omp = _declare(C.CDLL(build_omp()))
+    return _lib_omp
+
+
+def _declare(L):
+    """Argument and result types of the oracle's C functions on library L."""
+    L.orc_spline_coeffs.argtypes = [C.c_int32, C.c_double, _dp, C.c_int32, C.c_double,
+                                    C.c_int32, C.c_double, _dp]
+    L.orc_spline_coeffs.restype = C.c_int
+    L.orc_spline_eval.argtypes = [C.c_int32, C.c_double, C.c_double, _dp, C.c_double, _dp, _dp]
+    L.orc_spline_eval.restype = C.c_double
+    L.orc_pot_create.argtypes = [C.c_int32, _dp, C.POINTER(_Knots), C.POINTER(_Knots),
+                                 C.POINTER(_Knots), C.c_double, C.c_double]
+    L.orc_pot_create.restype = C.c_void_p
+    L.orc_pot_destroy.argtypes = [C.c_void_p]
+    L.orc_wrap.argtypes = [C.c_int64, _dp, C.c_int, _dp]
+    L.orc_cell_dims.argtypes = [_dp, C.c_int, C.c_double, _ip]
+    L.orc_cell_dims.restype = C.c_int
+    L.orc_cells.argtypes = [C.c_int64, _dp, C.c_int, C.c_double, _dp, _ip, _ip]
+    L.orc_cells.restype = C.c_int
+    for name in ("orc_list_cells", "orc_list_brute"):
+        fn = getattr(L, name)
+        fn.argtypes = [C.c_int64, _dp, C.c_int, C.c_double, _dp, _lp, _ip, C.c_int64]
+        fn.restype = C.c_int64
+    L.orc_eam_eval.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int, _dp, _ip, _lp, _ip, _dp, _dp, _dp,
+                               _dp, _dp]
+    L.orc_eam_eval.restype = C.c_int
+    L.orc_sys_create.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int, _dp, _dp, _ip]
+    L.orc_sys_create.restype = C.c_void_p
+    L.orc_sys_destroy.argtypes = [C.c_void_p]
+    L.orc_sys_step.argtypes = [C.c_void_p, C.c_int64, C.c_double, C.c_int32]
+    L.orc_sys_step.restype = C.c_int
+    L.orc_sys_energy.argtypes = [C.c_void_p, _dp, _dp]
+    L.orc_sys_virial.argtypes = [C.c_void_p, _dp]
+    L.orc_sys_get.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, _dp, _lp]
+    L.orc_spline_basis.argtypes = [C.c_int32, C.c_double, C.c_int32, C.c_int32, _dp]
+    L.orc_spline_basis.restype = C.c_int
+    L.orc_force_match.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int, _dp, C.c_double, _dp, C.c_double,
+                                  _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_force_match.restype = C.c_int
+    return L
 
 
 def _d(a):
@@ -144,11 +171,13 @@ def spline_eval(knots, coef, x):
 
 
 class Potential:
-    """Owns the oracle's own coefficient tables for an `inputs.Potential`."""
+    """Owns the oracle's own coefficient tables for an `inputs.Potential`.
+    `L`: the oracle library to build them in (default the parity build)."""
 
-    def __init__(self, pot):
+    def __init__(self, pot, L=None):
         self.src = pot
         self._keep = []
+        self.L = L if L is not None else lib()
 
         def arr(ks):
             out = (_Knots * len(ks))()
@@ -160,7 +189,7 @@ class Potential:
 
         self._mass = _f64(pot.mass)
         F, f, phi = arr(pot.F), arr(pot.f), arr(pot.phi)
-        self.handle = lib().orc_pot_create(pot.ntypes, _d(self._mass), F, f, phi, pot.r_cut, pot.skin)
+        self.handle = self.L.orc_pot_create(pot.ntypes, _d(self._mass), F, f, phi, pot.r_cut, pot.skin)
         if not self.handle:
             raise ValueError("oracle could not build the potential")
         self.r_cut = pot.r_cut
@@ -169,8 +198,8 @@ class Potential:
 
     def __del__(self):
         h = getattr(self, "handle", None)
-        if h and _lib is not None:
-            _lib.orc_pot_destroy(h)
+        if h and getattr(self, "L", None) is not None:
+            self.L.orc_pot_destroy(h)
             self.handle = None
 
 
@@ -252,29 +281,30 @@ class System:
 
     def __init__(self, pot: Potential, box, pos, vel, types, open_axes: int = 0):
         self.pot = pot
+        self.L = pot.L
         self.n = int(pos.shape[0])
         self._box = _f64(box)
         pos = _f64(pos)
         vel = _f64(vel) if vel is not None else np.zeros_like(pos)
         types = np.ascontiguousarray(types, dtype=np.int32)
-        self.handle = lib().orc_sys_create(pot.handle, self.n, _d(self._box), int(open_axes), _d(pos),
-                                           _d(vel), _i(types))
+        self.handle = self.L.orc_sys_create(pot.handle, self.n, _d(self._box), int(open_axes), _d(pos),
+                                            _d(vel), _i(types))
         if not self.handle:
             raise ValueError("oracle system create failed (box < 3 r_list?)")
 
     def step(self, nsteps: int, dt: float, rebuild_every: int = 10):
-        rc = lib().orc_sys_step(self.handle, nsteps, dt, rebuild_every)
+        rc = self.L.orc_sys_step(self.handle, nsteps, dt, rebuild_every)
         if rc:
             raise RuntimeError(f"oracle step failed ({rc})")
 
     def energy(self):
         pe, ke = C.c_double(), C.c_double()
-        lib().orc_sys_energy(self.handle, C.byref(pe), C.byref(ke))
+        self.L.orc_sys_energy(self.handle, C.byref(pe), C.byref(ke))
         return pe.value, ke.value
 
     def virial(self):
         w = np.zeros(6)
-        lib().orc_sys_virial(self.handle, _d(w))
+        self.L.orc_sys_virial(self.handle, _d(w))
         return w
 
     def state(self):
@@ -284,14 +314,14 @@ class System:
         rho = np.zeros(self.n)
         Fp = np.zeros(self.n)
         cnt = np.zeros(2, dtype=np.int64)
-        lib().orc_sys_get(self.handle, _d(pos), _d(vel), _d(force), _d(rho), _d(Fp), _l(cnt))
+        self.L.orc_sys_get(self.handle, _d(pos), _d(vel), _d(force), _d(rho), _d(Fp), _l(cnt))
         return dict(pos=pos, vel=vel, force=force, rho=rho, Fp=Fp, step=int(cnt[0]),
                     rebuilds=int(cnt[1]))
 
     def __del__(self):
         h = getattr(self, "handle", None)
-        if h and _lib is not None:
-            _lib.orc_sys_destroy(h)
+        if h and getattr(self, "L", None) is not None:
+            self.L.orc_sys_destroy(h)
             self.handle = None
 
 

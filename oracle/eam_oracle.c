@@ -27,6 +27,12 @@
  *     build or when some atom has moved more than skin/2 since then.
  *
  * Compile with -ffp-contract=off: every product and sum is rounded as written.
+ * The per-atom loops of the evaluation and the integrator carry OpenMP
+ * pragmas; the parity build ignores them (no -fopenmp: one thread, the sums
+ * in the order written).  A second build with -fopenmp is used only to time
+ * the oracle on all host cores; there the per-atom results are the same and
+ * only the sums over atoms (energies, virial, largest displacement) are
+ * taken in another order.  The list build stays serial in both.
  */
 #include <math.h>
 #include <stdint.h>
@@ -397,6 +403,7 @@ static double density_pass(const orc_pot *p, int64_t n, const double box[3], int
 {
     double rc2 = p->r_cut * p->r_cut;
     double e_embed = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : e_embed)
     for (int64_t i = 0; i < n; ++i) {
         double r_i = 0.0;
         for (int64_t q = off[i]; q < off[i + 1]; ++q) {
@@ -427,6 +434,7 @@ static double force_pass(const orc_pot *p, int64_t n, const double box[3], int o
     double rc2 = p->r_cut * p->r_cut;
     double e_pair = 0.0;
     for (int k = 0; k < 6; ++k) virial[k] = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : e_pair, virial[0:6])
     for (int64_t i = 0; i < n; ++i) {
         double fi[3] = {0.0, 0.0, 0.0};
         int32_t ti = types[i];
@@ -569,6 +577,7 @@ int orc_sys_step(orc_sys *s, int64_t nsteps, double dt, int32_t rebuild_every)
 {
     double half_skin2 = 0.25 * s->pot->skin * s->pot->skin;
     for (int64_t it = 0; it < nsteps; ++it) {
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < s->n; ++i) {
             double m = s->pot->mass[s->types[i]];
             for (int a = 0; a < 3; ++a) {
@@ -580,6 +589,7 @@ int orc_sys_step(orc_sys *s, int64_t nsteps, double dt, int32_t rebuild_every)
         s->step += 1;
         s->since_build += 1;
         double worst = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : worst)
         for (int64_t i = 0; i < s->n; ++i) {
             double dx = s->pos[3 * i] - s->x_ref[3 * i];
             double dy = s->pos[3 * i + 1] - s->x_ref[3 * i + 1];
@@ -593,6 +603,7 @@ int orc_sys_step(orc_sys *s, int64_t nsteps, double dt, int32_t rebuild_every)
         }
         int rc = evaluate(s);
         if (rc) return rc;
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < s->n; ++i) {
             double m = s->pot->mass[s->types[i]];
             for (int a = 0; a < 3; ++a) {

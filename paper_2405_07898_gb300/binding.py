@@ -58,7 +58,8 @@ class Options(C.Structure):
                 ("persistent", C.c_int32),
                 ("wait_limit_us", C.c_int32),
                 ("open_axes", C.c_int32),
-                ("batch_schedule", C.c_int32)]
+                ("batch_schedule", C.c_int32),
+                ("half_list", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -67,7 +68,7 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_int64), ("lanes_density", C.c_int32),
                 ("lanes_force", C.c_int32), ("threads_density", C.c_int32),
                 ("threads_force", C.c_int32), ("persistent_blocks", C.c_int32),
-                ("persistent_lanes", C.c_int32)]
+                ("persistent_lanes", C.c_int32), ("half_list", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -221,7 +222,7 @@ class MD:
     def __init__(self, system, precision: str = "mixed", rebuild_every: int = 10,
                  list_capacity: int = 0, use_graphs: bool = True, block_size: int = 256,
                  lanes_per_atom: int = 0, use_torch: bool | None = None, persistent: str = "auto",
-                 wait_limit_us: int = 0):
+                 wait_limit_us: int = 0, half_list: bool = False):
         L = load()
         self._L = L
         self.n = int(system.n)
@@ -236,6 +237,7 @@ class MD:
         opt.lanes_per_atom = lanes_per_atom
         opt.persistent = PERSIST[persistent]
         opt.wait_limit_us = wait_limit_us
+        opt.half_list = 1 if half_list else 0
         opt.open_axes = int(getattr(system, "open_axes", 0))
         self._keep = []
         if use_torch is None:

@@ -194,6 +194,11 @@ bool alloc_buffers(md_ctx *ctx, const std::vector<double> &rows, const std::vect
     ok = ok && alloc_n(ctx, B.block_sums, (size_t)(G.ncells + kScanBlock - 1) / kScanBlock + 1);
     ok = ok && alloc_n(ctx, B.partials, (size_t)kEnergySlots * std::max(ctx->L.pstride, 1));
     ok = ok && alloc_n(ctx, B.list, (size_t)ctx->L.cap * ctx->L.ld);
+    if (ctx->opt.half_list) {
+        ok = ok && alloc_n(ctx, B.acc_rho, n);
+        ok = ok && alloc_n(ctx, B.acc_f, 3 * n);
+        ok = ok && alloc_n(ctx, B.own, n);
+    }
     R4 *coef = nullptr, *coef2 = nullptr;
     Tables<R> *tab = nullptr;
     ok = ok && alloc_n(ctx, coef, rows.size() / 4);
@@ -223,6 +228,9 @@ bool alloc_buffers(md_ctx *ctx, const std::vector<double> &rows, const std::vect
     }
     if (cudaMemset(B.count, 0, sizeof(int) * ((size_t)G.ncells + 1)) != cudaSuccess) return false;
     if (cudaMemset(B.nnb, 0, sizeof(int) * n) != cudaSuccess) return false;
+    if (ctx->opt.half_list && (cudaMemset(B.acc_rho, 0, sizeof(unsigned long long) * n) != cudaSuccess ||
+                               cudaMemset(B.acc_f, 0, sizeof(unsigned long long) * 3 * n) != cudaSuccess))
+        return false;
     for (int a = 0; a < 3; ++a)
         if (cudaMemset(B.fcache[a], 0, sizeof(R) * n) != cudaSuccess) return false;
     return true;
@@ -961,6 +969,9 @@ md_status create_impl(md_ctx *ctx, const double *pos, const double *vel, const i
     if (trc != MD_OK) return trc;
     ctx->L.multi = tab.fused ? 0 : 1;
     ctx->L.nint_fused = tab.fused ? tab.fphi.nint : 0;
+    if (ctx->opt.half_list && (ctx->precision != MD_PRECISION_MIXED || ctx->L.multi))
+        return ctx->fail(MD_ERR_ARG, "half_list takes mixed precision and one atom type whose f and phi share a knot grid");
+    ctx->L.half = ctx->opt.half_list ? 1 : 0;
     ctx->shapes.clear();
     for (int t = 0; t < pot->ntypes; ++t) ctx->shapes.push_back(pot->F[t]);
     for (int t = 0; t < pot->ntypes; ++t) ctx->shapes.push_back(pot->f[t]);
@@ -984,6 +995,13 @@ md_status create_impl(md_ctx *ctx, const double *pos, const double *vel, const i
     md_status rc = load_and_measure<R>(ctx, pos, vel, 0);
     if (rc != MD_OK) return rc;
     const md_options &o = ctx->opt;
+    if (ctx->L.half) {
+        // one lane per atom, the context's block size; the graph path only
+        set_sched(ctx, PassSched{1, 0}, PassSched{1, 0});
+        rc = reevaluate<R>(ctx);
+        if (rc != MD_OK) return rc;
+        return check_device_errors(ctx);
+    }
     if (o.lanes_per_atom == 0) {
         rc = autotune<R>(ctx);
         if (rc != MD_OK) return rc;
@@ -1069,6 +1087,9 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     if (o.persistent < MD_PERSIST_AUTO || o.persistent > MD_PERSIST_ON)
         return bad(MD_ERR_ARG, "persistent must be MD_PERSIST_AUTO, _OFF or _ON");
     if (o.wait_limit_us < 0) return bad(MD_ERR_ARG, "wait_limit_us must be >= 0");
+    if (o.half_list != 0 && o.half_list != 1) return bad(MD_ERR_ARG, "half_list must be 0 or 1");
+    if (o.half_list && (o.persistent == MD_PERSIST_ON || o.lanes_per_atom > 1))
+        return bad(MD_ERR_ARG, "half_list runs as graphs with one lane per atom");
 
     md_ctx *ctx = new (std::nothrow) md_ctx();
     if (!ctx) return bad(MD_ERR_OOM, "host allocation failed");
@@ -1137,7 +1158,7 @@ md_status md_create(const double box[3], int64_t n, const double *pos, const dou
     }
     L.pstride = std::max(1, blocks_for_host(8 * n, std::min(L.block, 128)));
     {
-        int lanes = o.lanes_per_atom > 0 ? o.lanes_per_atom : 4;
+        int lanes = o.lanes_per_atom > 0 ? o.lanes_per_atom : (o.half_list ? 1 : 4);
         L.tpa_d = L.tpa_f = lanes;
         L.block_d = L.block_f = L.block;
         L.nb_d = L.nb_f = blocks_for_host(n * lanes, L.block);
@@ -1267,6 +1288,37 @@ md_status md_neighbors(md_ctx *ctx, int64_t *offsets, int32_t *js, int64_t cap)
     CK(cudaMemcpy(nnb.data(), nnbp, sizeof(int) * n, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(id.data(), idp, sizeof(int) * n, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(list.data(), lp, sizeof(uint32_t) * list.size(), cudaMemcpyDeviceToHost));
+    const size_t ld = (size_t)ctx->L.ld;
+    if (ctx->L.half) {
+        // each pair is listed once, by one of its atoms: give it to both
+        // ends (the other end's stencil code is the mirrored one, t -> 2 - t
+        // per axis), then order every list as the full-list build does,
+        // which is ascending entry value (stencil code in the high bits,
+        // sorted index below)
+        std::vector<std::vector<uint32_t>> full(n);
+        for (int64_t p = 0; p < n; ++p)
+            for (int k = 0; k < nnb[p]; ++k) {
+                const uint32_t e = list[(size_t)k * ld + p];
+                const uint32_t q = e & kIndexMask, c = e >> kCodeShift;
+                const uint32_t mc = (2u - (c & 3u)) | ((2u - ((c >> 2) & 3u)) << 2) | ((2u - (c >> 4)) << 4);
+                full[p].push_back(e);
+                full[q].push_back((uint32_t)p | (mc << kCodeShift));
+            }
+        std::vector<int64_t> cnt(n + 1, 0);
+        for (int64_t p = 0; p < n; ++p) {
+            std::sort(full[p].begin(), full[p].end());
+            cnt[id[p]] = (int64_t)full[p].size();
+        }
+        offsets[0] = 0;
+        for (int64_t i = 0; i < n; ++i) offsets[i + 1] = offsets[i] + cnt[i];
+        if (js && offsets[n] <= cap) {
+            for (int64_t p = 0; p < n; ++p) {
+                int64_t o = offsets[id[p]];
+                for (uint32_t e : full[p]) js[o++] = id[e & kIndexMask];
+            }
+        }
+        return MD_OK;
+    }
     std::vector<int64_t> cnt(n + 1, 0);
     for (int64_t p = 0; p < n; ++p) cnt[id[p]] = nnb[p];
     offsets[0] = 0;
@@ -1274,7 +1326,7 @@ md_status md_neighbors(md_ctx *ctx, int64_t *offsets, int32_t *js, int64_t cap)
     if (js && offsets[n] <= cap) {
         for (int64_t p = 0; p < n; ++p) {
             int64_t o = offsets[id[p]];
-            for (int k = 0; k < nnb[p]; ++k) js[o + k] = id[list[(size_t)k * ctx->L.ld + p] & kIndexMask];
+            for (int k = 0; k < nnb[p]; ++k) js[o + k] = id[list[(size_t)k * ld + p] & kIndexMask];
         }
     }
     return MD_OK;
@@ -1323,6 +1375,7 @@ md_status md_stats(md_ctx *ctx, md_stats_t *out)
     out->threads_force = ctx->L.block_f;
     out->persistent_blocks = ctx->persist_grid;
     out->persistent_lanes = ctx->persist_grid ? ctx->persist_tpa : 0;
+    out->half_list = ctx->L.half;
     return MD_OK;
 }
 

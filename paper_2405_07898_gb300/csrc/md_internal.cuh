@@ -18,6 +18,12 @@
 //                dz) of the neighbour's cell as t = d + 1 in {0, 1, 2} in
 //                bits 26..27 (x), 28..29 (y), 30..31 (z)
 //   nnb          int32 neighbours per atom
+//   acc_rho, acc_f  int64 per atom (density) and per atom and axis (force,
+//                interleaved xyz): fixed-point sums (2^-32 units) of the pair
+//                terms added to an atom from the other end of a half-list
+//                pair; zeroed by the pass that reads them (half lists only)
+//   own          float4 per atom: the sum of an atom's own half-list terms
+//                (density in x; force in x, y, z) (half lists only)
 // "set" flips at every list build (the permutation writes the other set),
 // "sp" flips at every drift.  Both live in DevState, on the device, so that a
 // captured CUDA graph replays correctly whatever the rebuild history.
@@ -128,6 +134,10 @@ struct Bufs {
     // list
     uint32_t *list;
     int *nnb;
+    // half lists: fixed-point accumulators and own partial sums
+    unsigned long long *acc_rho;
+    unsigned long long *acc_f;
+    float4 *own;
     // energy partials [kEnergySlots][nblocks]
     double *partials;
     // state and tables
@@ -154,6 +164,7 @@ struct Launch {
     int pstride;    // stride between energy slots in partials (>= nb_d, nb_f)
     int nint_fused; // intervals of the fused f|phi table (0: not fused)
     int multi;      // general type-dependent path (several types or unfused tables)
+    int half;       // 1: half lists (each pair once, j < i ends added through acc_*)
     int ntypes;
     int rebuild_every;
     double disp2_thr;                 // (skin/2)^2

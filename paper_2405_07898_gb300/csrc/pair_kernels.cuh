@@ -398,6 +398,216 @@ __global__ void __launch_bounds__(256) k_force(Bufs<R> B, Geom G, Launch L)
     force_block_end<R, ENERGY>(B, L, e7, ke, lane_sum<TPA>(d2), MODE == MODE_CLOSE_OPEN);
 }
 
+// ---- half lists (force symmetry): each pair once, the other end's term
+// added through fixed-point accumulators ----
+//
+// A pair (i, j) sits in one list only: that of the atom that sees the other
+// in the upper half space (the list build decides it exactly).  Its
+// density term f(r) (one type: the same for both ends) and its force term
+// s_ij (x_j - x_i)/r are formed once; i keeps its share in registers (a sum
+// in a fixed order, stored in own[i]), j's share goes into acc_*[j] as a
+// 64-bit integer in units of 2^-32 by an atomic add.  Integer sums do not
+// depend on the order of the adds, so the totals, and every result, are
+// bitwise reproducible.  A second pass per quantity adds own and acc (FP64),
+// zeroes acc for the next use, and carries on as the full-list passes do:
+// the embedding derivative F'(rho) into the record, or the integration.
+
+constexpr float kFixScale = 4294967296.0f;       // 2^32 fixed-point units per unit
+constexpr double kFixUnit = 1.0 / 4294967296.0;  // one unit
+constexpr float kFixLimit = 16777216.0f;         // 2^24: largest pair term the accumulators take
+
+__device__ __forceinline__ unsigned long long to_fixed(float x)
+{
+    return (unsigned long long)__float2ll_rn(x * kFixScale);
+}
+
+__device__ __forceinline__ double from_fixed(unsigned long long a)
+{
+    return (double)(long long)a * kFixUnit;
+}
+
+// rho_i's own terms and the scatter of j's; one lane per atom.
+__global__ void __launch_bounds__(256) k_density_half(Bufs<float> B, Geom G, Launch L)
+{
+    constexpr int U = 3;
+    float h[3];
+    load_h<float>(G, h);
+    const DevState *st = B.st;
+    const int sp = st->sp, s = st->set;
+    const float4 *sw = B.shadow[sp];
+    const int i0 = blockIdx.x * blockDim.x;
+    prefetch_warp_streams<float, false>(B, L, s, i0 + (threadIdx.x & ~31), 32, min(st->max_nnb, L.cap));
+    const int i = i0 + threadIdx.x;
+    if (i >= L.n) return;
+    const SplineDesc<float> g = B.tables->fphi;
+    const float rc2 = g_rc2<float>(G);
+    const float4 ui = sw[i];
+    const uint32_t *lp = B.list + i;
+    const int nn = B.nnb[i];
+    float rho = 0.f;
+    bool range_ok = true;
+    for (int k = 0; k < nn; k += U) {
+        uint32_t e[U];
+        float4 u[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) e[q] = (k + q < nn) ? lp[(size_t)(k + q) * L.ld] : 0u;
+#pragma unroll
+        for (int q = 0; q < U; ++q) u[q] = sw[(q == 0 || k + q < nn ? e[q] : e[0]) & kIndexMask];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const PairIn<float> pv = pair_vector<float>(ui, u[q], entry_shift<float>(e[q], h));
+            if ((q == 0 || k + q < nn) && pv.r2 < rc2) {
+                float rinv, r;
+                inv_r(pv.r2, rinv, r);
+                float t;
+                const int kk = segment(g, r, t);
+                const float4 c = B.coef_f[kk];
+                const float v = fma(t, fma(t, fma(t, c.w, c.z), c.y), c.x);
+                rho += v;
+                range_ok = range_ok && fabsf(v) < kFixLimit;
+                atomicAdd(B.acc_rho + (e[q] & kIndexMask), to_fixed(v));
+            }
+        }
+    }
+    if (!range_ok) atomicOr(&B.st->error, ERR_NONFINITE);
+    B.own[i].x = rho;
+}
+
+// rho_i = own + accumulated, F'(rho_i) into the record, F(rho_i) for the
+// energy; the accumulator is zeroed for the next pass.
+template <bool ENERGY>
+__global__ void __launch_bounds__(256) k_embed_half(Bufs<float> B, Launch L)
+{
+    const DevState *st = B.st;
+    float4 *sw = B.shadow[st->sp];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float e_embed = 0.f;
+    if (i < L.n) {
+        const double rho = (double)B.own[i].x + from_fixed(B.acc_rho[i]);
+        B.acc_rho[i] = 0ull;
+        e_embed = embed<float>(B, sw, i, 0, (float)rho);
+    }
+    if (ENERGY) {
+        const float v[1] = {e_embed};
+        block_sums_t<1, float>(v, B.partials, L.pstride, 0);
+    }
+}
+
+// F_i's own terms of Eq. 4 and the scatter of j's (-s_ij d / r); with ENERGY
+// the pair energy phi(r) and the virial of each pair, counted once.
+template <bool ENERGY>
+__global__ void __launch_bounds__(256) k_force_half(Bufs<float> B, Geom G, Launch L)
+{
+    constexpr int U = 2;
+    float h[3];
+    load_h<float>(G, h);
+    const DevState *st = B.st;
+    const int sp = st->sp, s = st->set;
+    const float4 *sw = B.shadow[sp];
+    const int i0 = blockIdx.x * blockDim.x;
+    prefetch_warp_streams<float, true>(B, L, s, i0 + (threadIdx.x & ~31), 32, min(st->max_nnb, L.cap));
+    const int i = i0 + threadIdx.x;
+    const SplineDesc<float> g = B.tables->fphi;
+    const float rc2 = g_rc2<float>(G);
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+    float e7[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (i < L.n) {
+        const float4 ui = sw[i];
+        const float Fpi = ui.w;
+        const uint32_t *lp = B.list + i;
+        const int nn = B.nnb[i];
+        bool range_ok = true;
+        for (int k = 0; k < nn; k += U) {
+            uint32_t e[U];
+            float4 u[U];
+#pragma unroll
+            for (int q = 0; q < U; ++q) e[q] = (k + q < nn) ? lp[(size_t)(k + q) * L.ld] : 0u;
+#pragma unroll
+            for (int q = 0; q < U; ++q) u[q] = sw[(q == 0 || k + q < nn ? e[q] : e[0]) & kIndexMask];
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const PairIn<float> pv = pair_vector<float>(ui, u[q], entry_shift<float>(e[q], h));
+                if ((q == 0 || k + q < nn) && pv.r2 < rc2) {
+                    float rinv, r;
+                    inv_r(pv.r2, rinv, r);
+                    float t;
+                    const int kk = segment(g, r, t);
+                    float4 cf, cp;
+                    load_row2<float>(B.coef2 + 2 * kk, cf, cp);
+                    const float fd = fma(t, fma(t, 3.f * cf.w, 2.f * cf.z), cf.y);
+                    const float pd = fma(t, fma(t, 3.f * cp.w, 2.f * cp.z), cp.y);
+                    const float sr = fma(u[q].w + Fpi, fd, pd) * rinv;
+                    const float gx = sr * pv.dx, gy = sr * pv.dy, gz = sr * pv.dz;
+                    f0 += gx;
+                    f1 += gy;
+                    f2 += gz;
+                    range_ok = range_ok && fabsf(gx) < kFixLimit && fabsf(gy) < kFixLimit && fabsf(gz) < kFixLimit;
+                    unsigned long long *aj = B.acc_f + 3 * (size_t)(e[q] & kIndexMask);
+                    atomicAdd(aj + 0, to_fixed(-gx));
+                    atomicAdd(aj + 1, to_fixed(-gy));
+                    atomicAdd(aj + 2, to_fixed(-gz));
+                    if (ENERGY) {
+                        e7[0] += fma(t, fma(t, fma(t, cp.w, cp.z), cp.y), cp.x);
+                        const float hs = -sr;
+                        e7[1] = fma(hs * pv.dx, pv.dx, e7[1]);
+                        e7[2] = fma(hs * pv.dy, pv.dy, e7[2]);
+                        e7[3] = fma(hs * pv.dz, pv.dz, e7[3]);
+                        e7[4] = fma(hs * pv.dx, pv.dy, e7[4]);
+                        e7[5] = fma(hs * pv.dx, pv.dz, e7[5]);
+                        e7[6] = fma(hs * pv.dy, pv.dz, e7[6]);
+                    }
+                }
+            }
+        }
+        if (!range_ok) atomicOr(&B.st->error, ERR_NONFINITE);
+        B.own[i] = make_float4(f0, f1, f2, 0.f);
+    }
+    if (ENERGY) {
+        const float pe[1] = {e7[0]};
+        block_sums_t<1, float>(pe, B.partials, L.pstride, 1);
+        const float w6[6] = {e7[1], e7[2], e7[3], e7[4], e7[5], e7[6]};
+        block_sums_t<6, float>(w6, B.partials, L.pstride, 3);
+    }
+}
+
+// F_i = own + accumulated (zeroed for the next pass), then the integration
+// of the full-list force pass (kicks, drift, next record, cached forces,
+// kinetic energy and largest displacement as MODE asks).
+template <int MODE, bool ENERGY>
+__global__ void __launch_bounds__(256) k_integrate_half(Bufs<float> B, Launch L)
+{
+    const DevState *st = B.st;
+    const int sp = st->sp, s = st->set;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double ke = 0.0;
+    float d2 = 0.f;
+    if (i < L.n) {
+        const float4 o = B.own[i];
+        unsigned long long *ai = B.acc_f + 3 * (size_t)i;
+        const float f[3] = {(float)((double)o.x + from_fixed(ai[0])), (float)((double)o.y + from_fixed(ai[1])),
+                            (float)((double)o.z + from_fixed(ai[2]))};
+        ai[0] = 0ull;
+        ai[1] = 0ull;
+        ai[2] = 0ull;
+        integrate<float, MODE, ENERGY, 1>(B, L, s, sp, i, 0, 0, f, ke, d2);
+    }
+    if (ENERGY) {
+        const float ke_hi = (float)ke;
+        const float v[1] = {ke_hi};
+        const float lo[1] = {(float)(ke - (double)ke_hi)};
+        block_sums_t<1, float>(v, B.partials, L.pstride, 2, lo);
+    }
+    if (MODE == MODE_CLOSE_OPEN) block_max_disp(d2, &B.st->maxdisp2);
+}
+
+template <int MODE, bool ENERGY>
+void force_half(const Bufs<float> &B, const Geom &G, const Launch &L)
+{
+    dim3 g(L.nb_f), b(L.block_f);
+    k_force_half<ENERGY><<<g, b, 0, L.stream>>>(B, G, L);
+    k_integrate_half<MODE, ENERGY><<<g, b, 0, L.stream>>>(B, L);
+}
+
 // ---- dispatch ----
 
 template <class R, bool MULTI, bool ENERGY>
@@ -444,6 +654,15 @@ void force_modes(const Bufs<R> &B, const Geom &G, const Launch &L, int mode, boo
 template <class R>
 int launch_density(const Bufs<R> &B, const Geom &G, const Launch &L, bool energy)
 {
+    if constexpr (std::is_same<R, float>::value) {
+        if (L.half) {
+            dim3 g(L.nb_d), b(L.block_d);
+            k_density_half<<<g, b, 0, L.stream>>>(B, G, L);
+            if (energy) k_embed_half<true><<<g, b, 0, L.stream>>>(B, L);
+            else k_embed_half<false><<<g, b, 0, L.stream>>>(B, L);
+            return 2;
+        }
+    }
     if (L.multi) {
         if (energy) density_tpa<R, true, true>(B, G, L);
         else density_tpa<R, true, false>(B, G, L);
@@ -457,6 +676,21 @@ int launch_density(const Bufs<R> &B, const Geom &G, const Launch &L, bool energy
 template <class R>
 int launch_force(const Bufs<R> &B, const Geom &G, const Launch &L, int mode, bool energy)
 {
+    if constexpr (std::is_same<R, float>::value) {
+        if (L.half) {
+            if (mode == MODE_MEASURE) {
+                if (energy) force_half<MODE_MEASURE, true>(B, G, L);
+                else force_half<MODE_MEASURE, false>(B, G, L);
+            } else if (mode == MODE_CLOSE) {
+                if (energy) force_half<MODE_CLOSE, true>(B, G, L);
+                else force_half<MODE_CLOSE, false>(B, G, L);
+            } else {
+                if (energy) force_half<MODE_CLOSE_OPEN, true>(B, G, L);
+                else force_half<MODE_CLOSE_OPEN, false>(B, G, L);
+            }
+            return 2;
+        }
+    }
     if (L.multi) force_modes<R, true>(B, G, L, mode, energy);
     else force_modes<R, false>(B, G, L, mode, energy);
     return 1;

@@ -130,12 +130,12 @@ __global__ void k_rebuild_finish(Bufs<R> B, int in_graph)
 }
 
 template <class R>
-__global__ void __launch_bounds__(256) k_build_list(Bufs<R> B, Geom G, int n, int ld, int cap)
+__global__ void __launch_bounds__(256) k_build_list(Bufs<R> B, Geom G, int n, int ld, int cap, int half)
 {
     DevState *st = B.st;
     if (!st->need_rebuild) return;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    const int cnt = (p < n) ? list_atom<R>(B, G, st->set, st->sp, p, ld, cap) : 0;
+    const int cnt = (p < n) ? list_atom<R>(B, G, st->set, st->sp, p, ld, cap, half != 0) : 0;
     block_max_nnb(cnt, &st->max_nnb);
 }
 
@@ -235,7 +235,7 @@ int launch_rebuild(const Bufs<R> &B, const Geom &G, const Launch &L)
     k_cell_sort<R><<<blocks_for(G.ncells, 256), 256, 0, L.stream>>>(B, G.ncells);
     k_permute<R><<<nb, b, 0, L.stream>>>(B, G, L.n);
     k_rebuild_finish<R><<<1, 1, 0, L.stream>>>(B, L.use_cond);
-    k_build_list<R><<<blocks_for(L.n, L.list_block), L.list_block, 0, L.stream>>>(B, G, L.n, L.ld, L.cap);
+    k_build_list<R><<<blocks_for(L.n, L.list_block), L.list_block, 0, L.stream>>>(B, G, L.n, L.ld, L.cap, L.half);
     return 8;
 }
 

@@ -182,6 +182,37 @@ __device__ __forceinline__ bool exact_in_list(const double *const xr[3], int p, 
     return r2 < G.rl2;
 }
 
+// Whether the pair vector d = x_q - x_p (minimum image) lies in the upper
+// half space: d_z > 0, or d_z = 0 and d_y > 0, or d_z = d_y = 0 and d_x > 0.
+// (dx, dy, dz) is the R-precision vector of the screen; where d_z is clearly
+// away from zero (far beyond its rounding error) it decides, elsewhere the
+// FP64 components of the definition do.  FP64 subtraction and the image
+// shift are exactly antisymmetric, so the answers for (p, q) and (q, p) are
+// complements: a pair is kept by exactly one of its atoms.
+template <class R>
+__device__ __forceinline__ bool upper_half(R dx, R dy, R dz, const double *const xr[3], int p, int q,
+                                           const Geom &G)
+{
+    (void)dx;
+    (void)dy;
+    const R tol = (R)1e-4;
+    if (dz > tol) return true;
+    if (dz < -tol) return false;
+    double d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double x = __dsub_rn(xr[a][q], xr[a][p]);
+        if (!((G.open_mask >> a) & 1)) {
+            if (x > G.half_box[a]) x = __dsub_rn(x, G.box[a]);
+            else if (x < -G.half_box[a]) x = __dadd_rn(x, G.box[a]);
+        }
+        d[a] = x;
+    }
+    if (d[2] != 0.0) return d[2] > 0.0;
+    if (d[1] != 0.0) return d[1] > 0.0;
+    return d[0] > 0.0;
+}
+
 // Verlet list of atom p: the atoms of the 27 surrounding cells (in stencil
 // order, ascending id inside a cell; cells beyond an open edge do not exist)
 // closer than r_list.  The test runs in R
@@ -190,9 +221,13 @@ __device__ __forceinline__ bool exact_in_list(const double *const xr[3], int p, 
 // FP64 definition.  The 9 rows of the stencil are unrolled; the 3 cells of a
 // row are a loop (a fully unrolled stencil outgrows the instruction cache).
 // Returns the neighbour count (the list keeps at most cap of them; more
-// raises ERR_LIST_OVERFLOW).
+// raises ERR_LIST_OVERFLOW).  half: keep each pair once, in the same order:
+// only the neighbours q whose pair vector x_q - x_p lies in the upper half
+// space (upper_half).  Every atom's neighbourhood is close to centrally
+// symmetric, so each lists about half its neighbours.
 template <class R>
-__device__ __forceinline__ int list_atom(const Bufs<R> &B, const Geom &G, int s, int sp, int p, int ld, int cap)
+__device__ __forceinline__ int list_atom(const Bufs<R> &B, const Geom &G, int s, int sp, int p, int ld, int cap,
+                                         bool half = false)
 {
     using R4 = typename V4<R>::T;
     int cnt = 0;
@@ -237,6 +272,7 @@ __device__ __forceinline__ int list_atom(const Bufs<R> &B, const Geom &G, int s,
                     const R ddx = uq.x + ox, ddy = uq.y + oy, ddz = uq.z + oz;
                     const R r2 = fma(ddz, ddz, fma(ddy, ddy, ddx * ddx));
                     if (r2 > hi || q == p) continue;
+                    if (half && !upper_half(ddx, ddy, ddz, xr, p, q, G)) continue;
                     if (r2 < lo || exact_in_list(xr, p, q, G)) {
                         if (cnt < cap) lp[(size_t)cnt * ld] = (uint32_t)q | code;
                         ++cnt;
