@@ -521,27 +521,10 @@ def run_model(args):
                      "density_ns_per_atom": 1e6 * prof["density_ms"] / n,
                      "force_ns_per_atom": 1e6 * prof["force_ms"] / n,
                      "build_ns_per_atom": 1e6 * prof["rebuild_ms"] / n})
-    A = np.array([[r["n_list"], r["n_inter"], 1.0] for r in rows])
-    Ab = np.array([[r["n_cand"], r["n_list"], 1.0] for r in rows])
-
-    def fit(M, key):
-        y = np.array([r[key] for r in rows])
-        c, *_ = np.linalg.lstsq(M, y, rcond=None)
-        pred = M @ c
-        r2 = 1.0 - float(((y - pred) ** 2).sum() / ((y - y.mean()) ** 2).sum())
-        return [float(v) for v in c], r2
-
-    (a, b, c), r2 = fit(A, "pair_ns_per_atom")
-    (ad, bd, cd), r2d = fit(A, "density_ns_per_atom")
-    (af, bf, cf), r2f = fit(A, "force_ns_per_atom")
-    (ab, bb, cb), r2b = fit(Ab, "build_ns_per_atom")
+    from paper_2405_07898_gb300 import timemodel
+    fits = timemodel.fit_points(rows)
     print(json.dumps({"workload": "linear_time_model_bcc_799496_mixed", "unit": "ns per atom",
-                      "points": rows,
-                      "pair_passes": {"per_list_entry": a, "per_interaction": b, "fixed": c, "r2": r2},
-                      "density": {"per_list_entry": ad, "per_interaction": bd, "fixed": cd, "r2": r2d},
-                      "force": {"per_list_entry": af, "per_interaction": bf, "fixed": cf, "r2": r2f},
-                      "list_build": {"per_candidate": ab, "per_list_entry": bb, "fixed": cb, "r2": r2b}}),
-          flush=True)
+                      "points": rows, **fits}), flush=True)
 
 
 def run_drift(args):

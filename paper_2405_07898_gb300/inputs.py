@@ -452,15 +452,16 @@ def sweep_systems(temperature: float = 1000.0):
 
 
 def sigma5_bicrystal(periods=(25, 10, 25), temperature: float = 1000.0, seed: int = SEED_BASE + 500,
-                     min_sep: float = 0.3) -> System:
+                     min_sep: float = 0.3, sigma: float = 0.02) -> System:
     """Sigma-5 (310)[001] symmetric tilt bicrystal of the BCC stand-in: two
     grains rotated by -+atan(1/3) (18.43 degrees) about z, so that [310] of
     the lower grain and [3-10] of the upper grain both lie along x.  One
     periodic cell of a grain is a sqrt(10) x a sqrt(10) x a with 20 atoms; the
     box holds periods[0] x (2 periods[1]) x periods[2] of them, the grains
     stacked along y (boundaries at y = 0 and y = L_y / 2).  Upper-grain atoms
-    closer than min_sep * a to a lower-grain atom are removed.  Thermal
-    displacements and Maxwell velocities at `temperature`."""
+    closer than min_sep * a to a lower-grain atom are removed.  Gaussian
+    displacements of `sigma` Angstrom and Maxwell velocities at
+    `temperature`."""
     p = BCC_TA_LIKE
     a = p.a
     s10 = math.sqrt(10.0)
@@ -497,7 +498,7 @@ def sigma5_bicrystal(periods=(25, 10, 25), temperature: float = 1000.0, seed: in
     upper = upper[dist >= min_sep * a]
     pos = inbox(np.vstack([lower, upper]))
     rng = np.random.Generator(np.random.PCG64(seed))
-    pos = displace(pos, box, 0.02, rng)
+    pos = displace(pos, box, sigma, rng)
     vel = maxwell(pos.shape[0], p.mass, temperature, rng)
     return System(box=box, pos=pos, vel=vel, types=np.zeros(pos.shape[0], np.int32),
                   pot=johnson_potential(p), label="sigma5_bicrystal")
