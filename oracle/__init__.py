@@ -101,6 +101,10 @@ def _declare(L):
     L.orc_eam_eval.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int, _dp, _ip, _lp, _ip, _dp, _dp, _dp,
                                _dp, _dp]
     L.orc_eam_eval.restype = C.c_int
+    L.orc_density.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int, _dp, _ip, _lp, _ip, _dp, _dp]
+    L.orc_density.restype = C.c_double
+    L.orc_force_given_fp.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int, _dp, _ip, _lp, _ip, _dp, _dp, _dp]
+    L.orc_force_given_fp.restype = C.c_double
     L.orc_sys_create.argtypes = [C.c_void_p, C.c_int64, _dp, C.c_int, _dp, _dp, _ip]
     L.orc_sys_create.restype = C.c_void_p
     L.orc_sys_destroy.argtypes = [C.c_void_p]
@@ -273,6 +277,32 @@ def eam_eval(pot: Potential, pos, box, types, off=None, js=None, open_axes: int 
     lib().orc_eam_eval(pot.handle, n, _d(_f64(box)), int(open_axes), _d(pos), _i(types), _l(off), _i(js),
                        _d(rho), _d(Fp), _d(force), _d(energy), _d(virial))
     return rho, Fp, force, energy, virial
+
+
+def density_pass(pot: Potential, pos, box, types, open_axes: int = 0):
+    """rho and F' of every atom (Eq. 2) over the 27-cell list of `pos`."""
+    pos = _f64(pos)
+    n = pos.shape[0]
+    off, js = neighbors_cells(pos, box, pot.r_list, open_axes)
+    rho = np.zeros(n)
+    Fp = np.zeros(n)
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    pot.L.orc_density(pot.handle, n, _d(_f64(box)), int(open_axes), _d(pos), _i(types), _l(off),
+                      _i(np.ascontiguousarray(js, dtype=np.int32)), _d(rho), _d(Fp))
+    return rho, Fp
+
+
+def force_pass(pot: Potential, pos, box, types, Fp, open_axes: int = 0):
+    """Forces of Eq. 4 with F' given for every atom."""
+    pos = _f64(pos)
+    n = pos.shape[0]
+    off, js = neighbors_cells(pos, box, pot.r_list, open_axes)
+    force = np.zeros((n, 3))
+    vir = np.zeros(6)
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    pot.L.orc_force_given_fp(pot.handle, n, _d(_f64(box)), int(open_axes), _d(pos), _i(types), _l(off),
+                             _i(np.ascontiguousarray(js, dtype=np.int32)), _d(_f64(Fp)), _d(force), _d(vir))
+    return force
 
 
 class System:

@@ -464,6 +464,25 @@ static double force_pass(const orc_pot *p, int64_t n, const double box[3], int o
     return e_pair;
 }
 
+/* The two passes of orc_eam_eval separately (the same functions): the
+ * density pass alone -- rho_i and F'_i of every atom of the list (Eq. 2);
+ * returns the embedding energy sum -- and the force pass with F' given for
+ * every atom (Eq. 4); returns the pair energy.  Used to check a spatial
+ * decomposition whose ranks exchange F' of their boundary atoms between the
+ * two passes. */
+double orc_density(const orc_pot *p, int64_t n, const double box[3], int open, const double *pos,
+                   const int32_t *types, const int64_t *off, const int32_t *js, double *rho, double *Fp)
+{
+    return density_pass(p, n, box, open, pos, types, off, js, rho, Fp);
+}
+
+double orc_force_given_fp(const orc_pot *p, int64_t n, const double box[3], int open, const double *pos,
+                          const int32_t *types, const int64_t *off, const int32_t *js, const double *Fp,
+                          double *force, double virial[6])
+{
+    return force_pass(p, n, box, open, pos, types, off, js, Fp, force, virial);
+}
+
 /* Density, forces, energies and virial for positions `pos` and a
  * neighbour list built for them (or for positions within skin/2 of them).
  * Any output pointer may be NULL except force. */
