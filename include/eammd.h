@@ -144,7 +144,7 @@ enum { MD_PERSIST_AUTO = 0, MD_PERSIST_OFF = 1, MD_PERSIST_ON = 2 };
  *                    512 x 1, 256 x 2, 256 x 3, 1024 x 1, 512 x 2.
  *   half_list        0: every atom lists all its neighbours and each pair is
  *                    evaluated from both ends (the default).  1: the
- *                    force-symmetry form (Section "Future Work"): each pair
+ *                    force-symmetry form (Section "Additional Acceleration"): each pair
  *                    is listed once -- by the atom that sees the other in
  *                    the upper half space (pair vector with d_z > 0, ties
  *                    broken by d_y, then d_x, decided exactly) -- and

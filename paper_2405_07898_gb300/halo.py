@@ -1,7 +1,7 @@
 """Spatial decomposition of one periodic system over ranks (one process per
-GPU): the multi-device counterpart of the paper's multi-wafer ghost model
-(Section "Multi-wafer"), where each wafer keeps copies of the atoms near its
-edge that its neighbours own.
+GPU): the multi-device counterpart of the paper's ghost model for many
+wafers (Section "Weak Scaling to Many Wafers"), where each node keeps copies
+of the atoms near its edge that its neighbours own.
 
 Each rank owns the atoms of a slab along one axis (z by default) and, per
 timestep:
