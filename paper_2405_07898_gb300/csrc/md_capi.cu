@@ -158,6 +158,44 @@ Bufs<float> &bufs<float>(md_ctx *ctx) { return ctx->Bf; }
 template <>
 Bufs<double> &bufs<double>(md_ctx *ctx) { return ctx->Bd; }
 
+// Texture objects over the two FP32 record buffers, for the density pass's
+// gathers.  Where the buffers do not meet the texture rules (alignment, the
+// largest linear texture), none is made and the density pass gathers through
+// the load path; both paths read the same words.
+void make_record_textures(Bufs<float> &B, size_t n)
+{
+    int dev = 0, align = 0, maxw = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&align, cudaDevAttrTextureAlignment, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture1DLinearWidth, dev) != cudaSuccess)
+        return;
+    if (n > (size_t)maxw) return;
+    unsigned long long t[2] = {0, 0};
+    for (int s = 0; s < 2; ++s) {
+        if (align <= 0 || (reinterpret_cast<uintptr_t>(B.shadow[s]) % (uintptr_t)align) != 0) break;
+        cudaResourceDesc rd{};
+        rd.resType = cudaResourceTypeLinear;
+        rd.res.linear.devPtr = B.shadow[s];
+        rd.res.linear.desc = cudaCreateChannelDesc<float4>();
+        rd.res.linear.sizeInBytes = n * sizeof(float4);
+        cudaTextureDesc td{};
+        td.readMode = cudaReadModeElementType;
+        td.filterMode = cudaFilterModePoint;
+        td.normalizedCoords = 0;
+        cudaTextureObject_t obj = 0;
+        if (cudaCreateTextureObject(&obj, &rd, &td, nullptr) != cudaSuccess) break;
+        t[s] = (unsigned long long)obj;
+    }
+    if (t[0] && t[1]) {
+        B.tex_shadow[0] = t[0];
+        B.tex_shadow[1] = t[1];
+        return;
+    }
+    for (int s = 0; s < 2; ++s)
+        if (t[s]) cudaDestroyTextureObject((cudaTextureObject_t)t[s]);
+    (void)cudaGetLastError();  // a refused texture is not an error of this context
+}
+
 template <class R>
 bool alloc_buffers(md_ctx *ctx, const std::vector<double> &rows, const std::vector<double> &rows2,
                    const Tables<R> &tables)
@@ -226,6 +264,8 @@ bool alloc_buffers(md_ctx *ctx, const std::vector<double> &rows, const std::vect
         if (cudaMemcpy(B.center[a], c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
             return false;
     }
+    B.tex_shadow[0] = B.tex_shadow[1] = 0;
+    if constexpr (std::is_same<R, float>::value) make_record_textures(B, n);
     if (cudaMemset(B.count, 0, sizeof(int) * ((size_t)G.ncells + 1)) != cudaSuccess) return false;
     if (cudaMemset(B.nnb, 0, sizeof(int) * n) != cudaSuccess) return false;
     if (ctx->opt.half_list && (cudaMemset(B.acc_rho, 0, sizeof(unsigned long long) * n) != cudaSuccess ||
@@ -1431,6 +1471,8 @@ void md_destroy(md_ctx *ctx)
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     drop_graphs(ctx);
+    for (int s = 0; s < 2; ++s)
+        if (ctx->Bf.tex_shadow[s]) cudaDestroyTextureObject((cudaTextureObject_t)ctx->Bf.tex_shadow[s]);
     dfree_all(ctx);
     if (ctx->st_host) cudaFreeHost(ctx->st_host);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);

@@ -120,6 +120,13 @@ struct Bufs {
     int *type[2];
     R *uref[3];
     R4 *shadow[2];
+    // texture objects over shadow[0] and shadow[1] (FP32 records only; 0 =
+    // none): the density pass gathers its neighbours' records through the
+    // texture path, which issues them at fewer L1 data-pipe cycles than the
+    // load path.  The density pass writes only the F' word of the records,
+    // which its gathers do not use, so the non-coherent texture reads of the
+    // coordinates are exact.
+    unsigned long long tex_shadow[2];
     R *fcache[3];
     int *cell;
     double *center[3];   // cell centres per axis, (c + 1/2) h_d

@@ -68,6 +68,15 @@ struct GlobalFetch {
     __device__ __forceinline__ typename V4<R>::T operator()(uint32_t e) const { return sw[e & kIndexMask]; }
 };
 
+// The same, through the texture path (FP32 records, density pass).
+struct TexFetch {
+    cudaTextureObject_t t;
+    __device__ __forceinline__ float4 operator()(uint32_t e) const
+    {
+        return tex1Dfetch<float4>(t, (int)(e & kIndexMask));
+    }
+};
+
 // Where the spline rows of the one-type path are read from: coef2 in device
 // memory (row 2k: f, row 2k+1: phi, both in one 32-byte load); the density
 // pass reads the f rows alone from coef_f, where a 128-byte line holds eight
@@ -338,7 +347,7 @@ template <bool MULTI> struct PairsInFlight {
     static constexpr int force = 2;
 };
 
-template <class R, bool MULTI, bool ENERGY, int TPA>
+template <class R, bool MULTI, bool ENERGY, int TPA, bool TEX>
 __global__ void __launch_bounds__(256) k_density(Bufs<R> B, Geom G, Launch L)
 {
     using R4 = typename V4<R>::T;
@@ -356,9 +365,17 @@ __global__ void __launch_bounds__(256) k_density(Bufs<R> B, Geom G, Launch L)
     const int ti = (MULTI && active) ? B.type[s][i] : 0;
     const R rc2 = g_rc2<R>(G);
     R rho = (R)0;
-    if (active)
-        rho = density_lane<R, MULTI, TPA, U>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i], ListGlobal{B.list + i, L.ld},
-                                             GlobalFetch<R>{sw}, TabGlobal<R>{B.coef2, B.coef_f});
+    if (active) {
+        if constexpr (TEX)
+            rho = density_lane<R, MULTI, TPA, U>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i],
+                                                 ListGlobal{B.list + i, L.ld},
+                                                 TexFetch{(cudaTextureObject_t)B.tex_shadow[sp]},
+                                                 TabGlobal<R>{B.coef2, B.coef_f});
+        else
+            rho = density_lane<R, MULTI, TPA, U>(B, h, rc2, s, B.nnb + i, L.cap, l, sw[i],
+                                                 ListGlobal{B.list + i, L.ld}, GlobalFetch<R>{sw},
+                                                 TabGlobal<R>{B.coef2, B.coef_f});
+    }
     rho = lane_sum<TPA>(rho);
     R e_embed = (R)0;
     if (active && l == 0) e_embed = embed<R>(B, sw, i, ti, rho);
@@ -610,16 +627,30 @@ void force_half(const Bufs<float> &B, const Geom &G, const Launch &L)
 
 // ---- dispatch ----
 
-template <class R, bool MULTI, bool ENERGY>
-void density_tpa(const Bufs<R> &B, const Geom &G, const Launch &L)
+template <class R, bool MULTI, bool ENERGY, bool TEX>
+void density_tpa_fetch(const Bufs<R> &B, const Geom &G, const Launch &L)
 {
     dim3 g(L.nb_d), b(L.block_d);
     switch (L.tpa_d) {
-    case 1: k_density<R, MULTI, ENERGY, 1><<<g, b, 0, L.stream>>>(B, G, L); break;
-    case 2: k_density<R, MULTI, ENERGY, 2><<<g, b, 0, L.stream>>>(B, G, L); break;
-    case 4: k_density<R, MULTI, ENERGY, 4><<<g, b, 0, L.stream>>>(B, G, L); break;
-    default: k_density<R, MULTI, ENERGY, 8><<<g, b, 0, L.stream>>>(B, G, L); break;
+    case 1: k_density<R, MULTI, ENERGY, 1, TEX><<<g, b, 0, L.stream>>>(B, G, L); break;
+    case 2: k_density<R, MULTI, ENERGY, 2, TEX><<<g, b, 0, L.stream>>>(B, G, L); break;
+    case 4: k_density<R, MULTI, ENERGY, 4, TEX><<<g, b, 0, L.stream>>>(B, G, L); break;
+    default: k_density<R, MULTI, ENERGY, 8, TEX><<<g, b, 0, L.stream>>>(B, G, L); break;
     }
+}
+
+// Records through the texture path where both record buffers have a texture
+// object (FP32), through the load path otherwise (FP64).
+template <class R, bool MULTI, bool ENERGY>
+void density_tpa(const Bufs<R> &B, const Geom &G, const Launch &L)
+{
+    if constexpr (std::is_same<R, float>::value) {
+        if (B.tex_shadow[0] && B.tex_shadow[1]) {
+            density_tpa_fetch<R, MULTI, ENERGY, true>(B, G, L);
+            return;
+        }
+    }
+    density_tpa_fetch<R, MULTI, ENERGY, false>(B, G, L);
 }
 
 template <class R, bool MULTI, int MODE, bool ENERGY>
