@@ -339,18 +339,42 @@ def _timed_steps(md, nsteps, dt, reps=1):
     return e0.elapsed_time(e1) * 1e-3
 
 
+def _oracle_steps(systems, nsteps: int):
+    """Seconds the serial FP64 oracle takes for nsteps timesteps of each
+    system (list builds included), and the atom-steps done."""
+    import oracle as O
+
+    total, atom_steps = 0.0, 0
+    for s in systems:
+        sysm = O.System(O.Potential(s.pot), s.box, s.pos, s.vel, s.types)
+        t0 = time.perf_counter()
+        sysm.step(nsteps, DT_FS)
+        total += time.perf_counter() - t0
+        atom_steps += s.n * nsteps
+    return total, atom_steps
+
+
 def run_sweep(args):
     """Strong-scaling sweep: BCC cubes of 1,024 .. 314,928 atoms and the
     799,496-atom box at 1,000 K (mixed precision): timesteps/s of md_step
     replayed as CUDA graphs, and up to 314,928 atoms as one cooperative launch
     per call (the library takes the single launch automatically up to 65,536
-    atoms)."""
+    atoms).  Beside each size, unless --no-cpu-baseline: the serial FP64
+    oracle on one host core, 100 timesteps up to 50,000 atoms and 10 above."""
     import torch
     from paper_2405_07898_gb300 import binding, inputs as I
 
+    # the oracle runs before the first GPU call
+    systems = I.sweep_systems(temperature=1000.0)
+    cpu = {}
+    if not args.no_cpu_baseline:
+        for s in systems:
+            k = 100 if s.n <= 50000 else 10
+            t, _ = _oracle_steps([s], k)
+            cpu[s.n] = (k, k / t)
     torch.cuda.set_device(0)
     rows = []
-    for s in I.sweep_systems(temperature=1000.0):
+    for s in systems:
         steps = max(200, min(20000, int(2e8 // s.n) // 10 * 10))
         row = {"atoms": s.n, "steps": steps}
         for mode in ("off", "on"):
@@ -367,6 +391,10 @@ def run_sweep(args):
                 row[key + "_blocks"] = st["persistent_blocks"]
                 row[key + "_lanes"] = st["persistent_lanes"]
             md.close()
+        if s.n in cpu:
+            row["oracle_steps"], row["oracle_ts_per_s"] = cpu[s.n]
+            row["oracle_atom_steps_per_s"] = s.n * cpu[s.n][1]
+            row["oracle_cores"] = 1
         rows.append(row)
     print(json.dumps({"workload": "bcc_sweep_1000K_mixed", "unit": "timesteps/s", "sweep": rows}), flush=True)
 
@@ -379,8 +407,17 @@ def run_batch(args):
     import torch
     from paper_2405_07898_gb300 import binding, inputs as I
 
-    torch.cuda.set_device(0)
     reps = I.replica_batch(512)
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle on every 32nd replica (8 BCC, 8 FCC), 10 steps each, before
+        # the first GPU call; its atom-steps/s stands for the whole batch
+        sample = reps[::32]
+        t, done = _oracle_steps(sample, 10)
+        cpu = {"value": done / t, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"10 timesteps of every 32nd replica ({len(sample)} replicas, "
+                         f"{sum(x.n for x in sample):,} atoms; serial FP64 C oracle), {t:.1f} s"}
+    torch.cuda.set_device(0)
     b = binding.MDBatch(reps)
     b.step(10, DT_FS)
     b.energy()
@@ -400,12 +437,15 @@ def run_batch(args):
     ms = e0.elapsed_time(e1)
     info = b.info()
     b.close()
-    print(json.dumps({"workload": "replicas_512_bcc_fcc_mixed", "metric": "atom-steps/s",
-                      "value": info["atoms"] * args.batch_steps / (ms * 1e-3), "unit": "atom-steps/s",
-                      "replicas": info["replicas"], "atoms": info["atoms"], "steps": args.batch_steps,
-                      "ms": ms, "kernel_launches": info["kernel_launches"] - info0["kernel_launches"],
-                      "blocks": info["blocks"], "threads_per_block": info["threads_per_block"],
-                      "rebuilds": info["rebuilds"] - info0["rebuilds"]}), flush=True)
+    line = {"workload": "replicas_512_bcc_fcc_mixed", "metric": "atom-steps/s",
+            "value": info["atoms"] * args.batch_steps / (ms * 1e-3), "unit": "atom-steps/s",
+            "replicas": info["replicas"], "atoms": info["atoms"], "steps": args.batch_steps,
+            "ms": ms, "kernel_launches": info["kernel_launches"] - info0["kernel_launches"],
+            "blocks": info["blocks"], "threads_per_block": info["threads_per_block"],
+            "rebuilds": info["rebuilds"] - info0["rebuilds"]}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
 
 
 def run_adjoint(args):
