@@ -90,10 +90,12 @@ __device__ __forceinline__ bool grid_barrier(PersistScratch *ps, unsigned *err, 
     return ok;
 }
 
-// Lanes per atom of the list build in the single launch, taken when one pass
-// of the grid covers all atoms; otherwise one thread walks each atom's
-// stencil.
-constexpr int kListLanes = 8;
+// The list build of the single launch: a warp per atom (list_atom_warp)
+// while the grid's warps cover the atoms in at most this many passes, else
+// one thread per atom (list_atom).  Measured on the BCC sweep: 8 passes
+// gains 5-14 % per step up to 18,522 atoms; 16 and 64 lose at 43,904 and
+// 118,638 atoms.
+constexpr int kListWarpPasses = 8;
 
 // One step loop of nsteps steps (nsteps >= 1).  The counters of DevState
 // (set, record buffer, steps since the build) advance identically in every
@@ -152,13 +154,18 @@ __global__ void __launch_bounds__(256) k_steps(Bufs<R> B, Geom G, Launch L, long
             since = 0;
             rebuilds += 1;
             if (!grid_barrier(ps, err, L.wait_ns)) return;
-            if ((long long)n * kListLanes <= nthreads) {
-                // kListLanes lanes per atom, all atoms in one pass
-                const int p = blockIdx.x * (blockDim.x / kListLanes) + threadIdx.x / kListLanes;
-                const int cnt =
-                    (p < n) ? list_atom_lanes<R, kListLanes>(B, G, s, sp, p, L.ld, L.cap, threadIdx.x % kListLanes)
-                            : 0;
-                block_max_nnb(cnt, &st->max_nnb);
+            if ((long long)n * 32 <= (long long)nthreads * kListWarpPasses) {
+                // a warp per atom, one lane per stencil cell; the grid's warps
+                // take the atoms in at most kListWarpPasses passes
+                const int nwarps = nthreads >> 5;
+                const int w0 = gtid >> 5;
+                int cmax = 0;
+                for (int base = 0; base < n; base += nwarps) {
+                    const int p = base + w0;
+                    // the warp's lanes share p, so the whole warp takes this branch
+                    if (p < n) cmax = max(cmax, list_atom_warp<R>(B, G, s, sp, p, L.ld, L.cap));
+                }
+                block_max_nnb(cmax, &st->max_nnb);
             } else {
                 for (int base = blockIdx.x * blockDim.x; base < n; base += nthreads) {
                     const int p = base + threadIdx.x;

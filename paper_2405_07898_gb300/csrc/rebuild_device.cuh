@@ -286,24 +286,24 @@ __device__ __forceinline__ int list_atom(const Bufs<R> &B, const Geom &G, int s,
     return cnt;
 }
 
-// list_atom with LT consecutive lanes of a warp on atom p (lane l of the
-// group; LT divides 32): the lanes take slots l, l + LT, ... of each stencil
-// cell, and a ballot over the group places the hits of a round in candidate
-// order, so the list is the one list_atom writes, entry for entry.  The walk
-// per atom is a chain of rounds (about one per cell) instead of one
-// iteration per candidate: the single-launch forms build the lists of a few
-// thousand atoms, where that chain is the whole cost of the build.  Every
-// lane returns the count.
-template <class R, int LT>
-__device__ __forceinline__ int list_atom_lanes(const Bufs<R> &B, const Geom &G, int s, int sp, int p, int ld,
-                                               int cap, int l)
+// list_atom with the 32 lanes of a warp on atom p: lane c < 27 walks
+// stencil cell c = 9 (dz + 1) + 3 (dy + 1) + (dx + 1) -- the stencil order --
+// issuing its candidates' record loads four at a time, and an exclusive warp
+// prefix sum of the cells' hit counts gives each cell its place in the list,
+// so the list is the one list_atom writes, entry for entry.  The walk per
+// atom is a few rounds of independent loads (the cells in parallel) instead
+// of a chain of ~27: for systems of a few thousand atoms, whose records were
+// just written by other SMs, the chain's L2 round trips are the cost of the
+// build.  A cell's decisions are kept as a bit mask for its first 64
+// candidates and recomputed beyond them.  All 32 lanes must call; every lane
+// returns the count.
+template <class R>
+__device__ __forceinline__ int list_atom_warp(const Bufs<R> &B, const Geom &G, int s, int sp, int p, int ld,
+                                              int cap)
 {
-    static_assert(LT >= 1 && LT <= 32 && (32 % LT) == 0, "lanes per atom must divide 32");
     using R4 = typename V4<R>::T;
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned gmask = LT == 32 ? 0xffffffffu : (((1u << LT) - 1u) << (lane & ~(unsigned)(LT - 1)));
-    const unsigned below = (1u << l) - 1u;
-    int cnt = 0;
+    constexpr int UQ = 4;  // candidate loads in flight per lane
+    const int lane = (int)(threadIdx.x & 31u);
     const double *const xr[3] = {B.xr[s][0], B.xr[s][1], B.xr[s][2]};
     const R4 *sw = B.shadow[sp];
     const R lo = g_screen_lo<R>(G), hi = g_screen_hi<R>(G);
@@ -312,58 +312,73 @@ __device__ __forceinline__ int list_atom_lanes(const Bufs<R> &B, const Geom &G, 
     const int cell = B.cell[p];
     const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
     const R4 up = sw[p];
+    const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
+    int ex = cx + dx, ey = cy + dy, ez = cz + dz;
+    bool valid = lane < 27;
+    if (ex < 0 || ex >= nx) {
+        if (G.open_mask & 1) valid = false;
+        else ex += (ex < 0) ? nx : -nx;
+    }
+    if (ey < 0 || ey >= ny) {
+        if ((G.open_mask >> 1) & 1) valid = false;
+        else ey += (ey < 0) ? ny : -ny;
+    }
+    if (ez < 0 || ez >= nz) {
+        if ((G.open_mask >> 2) & 1) valid = false;
+        else ez += (ez < 0) ? nz : -nz;
+    }
+    int q0 = 0, q1 = 0;
+    if (valid) {
+        const int e = (ez * ny + ey) * nx + ex;
+        q0 = B.cell_start[e];
+        q1 = B.cell_start[e + 1];
+    }
+    const R ox = (R)dx * hx - up.x, oy = (R)dy * hy - up.y, oz = (R)dz * hz - up.z;
+    auto in_list = [&](const R4 &uq, int q) -> bool {
+        const R ddx = uq.x + ox, ddy = uq.y + oy, ddz = uq.z + oz;
+        const R r2 = fma(ddz, ddz, fma(ddy, ddy, ddx * ddx));
+        return !(r2 > hi || q == p) && (r2 < lo || exact_in_list(xr, p, q, G));
+    };
+    unsigned long long bits = 0ull;
+    int hits = 0;
+    for (int q = q0; q < q1; q += UQ) {
+        R4 u[UQ];
+#pragma unroll
+        for (int k = 0; k < UQ; ++k) u[k] = sw[min(q + k, q1 - 1)];
+#pragma unroll
+        for (int k = 0; k < UQ; ++k) {
+            if (q + k < q1 && in_list(u[k], q + k)) {
+                if (q + k - q0 < 64) bits |= 1ull << (q + k - q0);
+                ++hits;
+            }
+        }
+    }
+    int incl = hits;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int pos = incl - hits;
     uint32_t *lp = B.list + p;
-    const bool open_x = G.open_mask & 1, open_y = (G.open_mask >> 1) & 1, open_z = (G.open_mask >> 2) & 1;
-#pragma unroll 1
-    for (int dz = -1; dz <= 1; ++dz) {
-        int ez = cz + dz;
-        if (ez < 0 || ez >= nz) {
-            if (open_z) continue;
-            ez += (ez < 0) ? nz : -nz;
-        }
-#pragma unroll 1
-        for (int dy = -1; dy <= 1; ++dy) {
-            int ey = cy + dy;
-            if (ey < 0 || ey >= ny) {
-                if (open_y) continue;
-                ey += (ey < 0) ? ny : -ny;
-            }
-            const int row = (ez * ny + ey) * nx;
-#pragma unroll 1
-            for (int dx = -1; dx <= 1; ++dx) {
-                int ex = cx + dx;
-                if (ex < 0 || ex >= nx) {
-                    if (open_x) continue;
-                    ex += (ex < 0) ? nx : -nx;
-                }
-                const int e = row + ex;
-                const uint32_t code = list_entry(0u, dx, dy, dz);
-                const R ox = (R)dx * hx - up.x, oy = (R)dy * hy - up.y, oz = (R)dz * hz - up.z;
-                const int q0 = B.cell_start[e], q1 = B.cell_start[e + 1];
-                for (int base = q0; base < q1; base += LT) {
-                    const int q = base + l;
-                    bool in = false;
-                    if (q < q1) {
-                        const R4 uq = sw[q];
-                        const R ddx = uq.x + ox, ddy = uq.y + oy, ddz = uq.z + oz;
-                        const R r2 = fma(ddz, ddz, fma(ddy, ddy, ddx * ddx));
-                        in = !(r2 > hi || q == p) && (r2 < lo || exact_in_list(xr, p, q, G));
-                    }
-                    const unsigned hits = (__ballot_sync(gmask, in) & gmask) >> (lane & ~(unsigned)(LT - 1));
-                    if (in) {
-                        const int pos = cnt + __popc(hits & below);
-                        if (pos < cap) lp[(size_t)pos * ld] = (uint32_t)q | code;
-                    }
-                    cnt += __popc(hits & (LT == 32 ? 0xffffffffu : ((1u << LT) - 1u)));
-                }
-            }
-        }
+    const uint32_t code = list_entry(0u, dx, dy, dz);
+    while (bits) {
+        const int k = __ffsll((long long)bits) - 1;
+        bits &= bits - 1ull;
+        if (pos < cap) lp[(size_t)pos * ld] = (uint32_t)(q0 + k) | code;
+        ++pos;
     }
-    if (l == 0) {
-        B.nnb[p] = min(cnt, cap);
-        if (cnt > cap) atomicOr(&B.st->error, ERR_LIST_OVERFLOW);
+    for (int q = q0 + 64; q < q1; ++q)
+        if (in_list(sw[q], q)) {
+            if (pos < cap) lp[(size_t)pos * ld] = (uint32_t)q | code;
+            ++pos;
+        }
+    if (lane == 0) {
+        B.nnb[p] = min(total, cap);
+        if (total > cap) atomicOr(&B.st->error, ERR_LIST_OVERFLOW);
     }
-    return cnt;
+    return total;
 }
 
 // Block maximum of the neighbour counts into st->max_nnb (one atomic per
