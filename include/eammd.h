@@ -249,7 +249,9 @@ typedef struct {
     int32_t persistent_blocks; /* blocks of the single-launch md_step (0: graphs) */
     int32_t persistent_lanes;  /* lanes per atom of its pair passes */
     int32_t half_list;         /* 1: pairs listed and evaluated once (md_options.half_list) */
-    int32_t reserved;
+    int32_t record_textures;   /* 1: the density pass gathers neighbour records through texture
+                                  objects (mixed precision, record buffers aligned for textures);
+                                  0: through ordinary loads.  Results are the same either way. */
 } md_stats_t;
 
 md_status md_stats(md_ctx *ctx, md_stats_t *out);

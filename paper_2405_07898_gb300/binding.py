@@ -68,7 +68,7 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_int64), ("lanes_density", C.c_int32),
                 ("lanes_force", C.c_int32), ("threads_density", C.c_int32),
                 ("threads_force", C.c_int32), ("persistent_blocks", C.c_int32),
-                ("persistent_lanes", C.c_int32), ("half_list", C.c_int32), ("reserved", C.c_int32)]
+                ("persistent_lanes", C.c_int32), ("half_list", C.c_int32), ("record_textures", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -216,13 +216,14 @@ class MD:
 
     `system` is an `inputs.System`.  precision: "mixed" or "fp64".
     With use_torch=True (default when CUDA is available to torch) device
-    memory comes from torch's caching allocator and work is queued on a
-    torch stream owned by this object (`self.stream`)."""
+    memory comes from torch's caching allocator, or from `allocator` =
+    (alloc(nbytes) -> device pointer or None, free(pointer)) when given, and
+    work is queued on a torch stream owned by this object (`self.stream`)."""
 
     def __init__(self, system, precision: str = "mixed", rebuild_every: int = 10,
                  list_capacity: int = 0, use_graphs: bool = True, block_size: int = 256,
                  lanes_per_atom: int = 0, use_torch: bool | None = None, persistent: str = "auto",
-                 wait_limit_us: int = 0, half_list: bool = False):
+                 wait_limit_us: int = 0, half_list: bool = False, allocator=None):
         L = load()
         self._L = L
         self.n = int(system.n)
@@ -250,7 +251,14 @@ class MD:
             import torch
             torch.cuda.init()
             self.stream = torch.cuda.Stream()
-            a, f = _torch_allocator(self.stream)
+            if allocator is None:
+                a, f = _torch_allocator(self.stream)
+            else:
+                # caller's device allocator: (alloc(nbytes) -> pointer or None,
+                # free(pointer)); pointers must be 256-byte aligned
+                ua, uf = allocator
+                a = ALLOC_FN(lambda nbytes, _ctx: ua(int(nbytes)))
+                f = FREE_FN(lambda ptr, _ctx: uf(int(ptr)))
             self._keep += [a, f]
             opt.alloc, opt.free = a, f
             opt.cuda_stream = C.c_void_p(self.stream.cuda_stream)
@@ -446,7 +454,14 @@ class MDBatch:
             import torch
             torch.cuda.init()
             self.stream = torch.cuda.Stream()
-            a, f = _torch_allocator(self.stream)
+            if allocator is None:
+                a, f = _torch_allocator(self.stream)
+            else:
+                # caller's device allocator: (alloc(nbytes) -> pointer or None,
+                # free(pointer)); pointers must be 256-byte aligned
+                ua, uf = allocator
+                a = ALLOC_FN(lambda nbytes, _ctx: ua(int(nbytes)))
+                f = FREE_FN(lambda ptr, _ctx: uf(int(ptr)))
             self._keep += [a, f]
             opt.alloc, opt.free = a, f
             opt.cuda_stream = C.c_void_p(self.stream.cuda_stream)

@@ -1416,6 +1416,7 @@ md_status md_stats(md_ctx *ctx, md_stats_t *out)
     out->persistent_blocks = ctx->persist_grid;
     out->persistent_lanes = ctx->persist_grid ? ctx->persist_tpa : 0;
     out->half_list = ctx->L.half;
+    out->record_textures = (ctx->precision == MD_PRECISION_MIXED && ctx->Bf.tex_shadow[0] && ctx->Bf.tex_shadow[1]) ? 1 : 0;
     return MD_OK;
 }
 

@@ -109,3 +109,47 @@ def test_block_sizes_give_the_same_forces(c1, block):
             np.testing.assert_array_equal(a.get_state()[0], b.get_state()[0])
             ea, eb = sum(a.energy()), sum(b.energy())
             assert abs(ea - eb) / abs(eb) < (1e-13 if precision == "fp64" else 1e-9)
+
+
+def _offset_allocator(offset=256):
+    """Device memory from torch's caching allocator, handed out `offset` bytes
+    past a 512-byte boundary: still 256-byte aligned as the C ABI requires,
+    but off the texture alignment of the device."""
+    import torch
+    bases = {}
+
+    def alloc(nbytes):
+        try:
+            base = torch.cuda.caching_allocator_alloc(nbytes + 512)
+        except Exception:
+            return None
+        p = base + offset
+        bases[p] = base
+        return p
+
+    def free(p):
+        torch.cuda.caching_allocator_delete(bases.pop(p))
+
+    return alloc, free
+
+
+def test_record_gathers_through_textures_or_loads_give_the_same_results():
+    """The density pass gathers neighbour records through texture objects
+    where the record buffers allow it, through ordinary loads otherwise:
+    the same words either way, so trajectories, forces and energies are
+    bitwise equal."""
+    s = I.thermal_system(I.BCC_TA_LIKE, (20, 20, 20), 0.02, 600.0, 31)
+    kw = dict(precision="mixed", persistent="off", lanes_per_atom=1)
+    with binding.MD(s, **kw) as a, binding.MD(s, allocator=_offset_allocator(), **kw) as b:
+        assert a.stats()["record_textures"] == 1
+        if b.stats()["record_textures"] == 1:
+            pytest.skip("this device takes textures on 256-byte aligned buffers")
+        for m in (a, b):
+            m.step(57, 2.0)
+        for x, y in zip(a.get_state(), b.get_state()):
+            np.testing.assert_array_equal(np.asarray(x), np.asarray(y))
+        np.testing.assert_array_equal(a.forces(), b.forces())
+        assert a.energy() == b.energy()
+        assert a.stats()["rebuilds"] == b.stats()["rebuilds"] > 0
+    with binding.MD(s, precision="fp64", persistent="off") as c:
+        assert c.stats()["record_textures"] == 0
