@@ -135,3 +135,44 @@ def test_wait_limit_raises_timeout_and_the_context_recovers():
     with pytest.raises(binding.MDError) as e:
         binding.MD(s, wait_limit_us=-1)
     assert e.value.status == -1
+
+
+def test_single_launch_list_build_with_crowded_cells():
+    """More than 64 atoms in a cell.  The single launch builds lists with a
+    warp per atom, a lane per stencil cell, keeping the decisions of a
+    cell's first 64 candidates as a bit mask and recomputing the rest: the
+    lists built inside the launch (a rebuild every step) must equal the
+    oracle's at the launch's own positions, and the graph path's (same lanes
+    per atom, so the same positions bit for bit)."""
+    rng = np.random.default_rng(64)
+    box = np.array([15.0, 15.0, 15.0])  # 3 x 3 x 3 cells of 5 A
+    cand = rng.random((8000, 3)) * box
+    keep = [cand[0]]
+    for x in cand[1:]:
+        d = np.asarray(keep) - x
+        d -= box * np.round(d / box)
+        if (d * d).sum(1).min() > 0.8**2:
+            keep.append(x)
+        if len(keep) == 2500:
+            break
+    pos = np.asarray(keep)
+    gas = I.System(box=box, pos=pos, vel=np.zeros_like(pos), types=np.zeros(len(pos), np.int32),
+                   pot=I.johnson_potential(I.BCC_TA_LIKE))
+    _, start, _ = O.cells(O.wrap(pos, box), box, gas.pot.r_list)
+    assert np.diff(start).max() > 64
+    for precision in ("mixed", "fp64"):
+        lists = []
+        for persistent in ("on", "off"):
+            with binding.MD(gas, precision=precision, persistent=persistent, rebuild_every=1,
+                            lanes_per_atom=1) as md:
+                assert (md.stats()["persistent_blocks"] > 0) == (persistent == "on")
+                md.step(3, 0.001)
+                assert md.stats()["rebuilds"] == 3
+                p, _, _ = md.get_state()
+                off, js = md.neighbors()
+            ooff, ojs = O.neighbors_cells(O.wrap(p, box), box, gas.pot.r_list)
+            np.testing.assert_array_equal(off, ooff)
+            np.testing.assert_array_equal(js, ojs)
+            lists.append((p, js))
+        np.testing.assert_array_equal(lists[0][0], lists[1][0])
+        np.testing.assert_array_equal(lists[0][1], lists[1][1])
