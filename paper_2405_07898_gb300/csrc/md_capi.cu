@@ -536,6 +536,9 @@ md_status profile_impl(md_ctx *ctx, int64_t nsteps, double dt, md_profile_t *out
     Launch L = ctx->L;
     L.use_cond = 0;
     L.cond = 0;
+    md_status rc0 = read_state(ctx);
+    if (rc0 != MD_OK) return rc0;
+    const long long rebuilds0 = ctx->st_host->rebuilds;
     const int64_t ne = 4 * nsteps + 2;
     std::vector<cudaEvent_t> ev(ne);
     for (auto &e : ev) CK(cudaEventCreate(&e));
@@ -558,19 +561,23 @@ md_status profile_impl(md_ctx *ctx, int64_t nsteps, double dt, md_profile_t *out
     CK(cudaStreamSynchronize(ctx->stream));
     double dens = 0, force = 0, reb = 0, total = 0;
     int64_t nreb = 0;
-    const double empty_rebuild_ms = 0.05;  // the 8 guarded kernels exit at once when no build is due
+    std::vector<float> span(nsteps);
     for (int64_t s = 0; s < nsteps; ++s) {
         float a = 0, b = 0, c = 0;
         CK(cudaEventElapsedTime(&a, ev[1 + 4 * s], ev[2 + 4 * s]));
         CK(cudaEventElapsedTime(&b, ev[2 + 4 * s], ev[3 + 4 * s]));
         CK(cudaEventElapsedTime(&c, ev[3 + 4 * s], ev[4 + 4 * s]));
-        if (a > empty_rebuild_ms) {
-            reb += a;
-            ++nreb;
-        }
+        span[s] = a;
         dens += b;
         force += c;
     }
+    // the 8 guarded rebuild kernels exit at once when no build is due: the
+    // device counted the builds, and they are the longest spans
+    md_status rc = read_state(ctx);
+    if (rc != MD_OK) return rc;
+    nreb = std::min<int64_t>(std::max<int64_t>(ctx->st_host->rebuilds - rebuilds0, 0), nsteps);
+    std::sort(span.begin(), span.end(), [](float x, float y) { return x > y; });
+    for (int64_t s = 0; s < nreb; ++s) reb += span[s];
     float tot = 0;
     CK(cudaEventElapsedTime(&tot, ev[0], ev[4 * nsteps]));
     total = tot;
