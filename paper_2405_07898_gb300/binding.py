@@ -454,14 +454,7 @@ class MDBatch:
             import torch
             torch.cuda.init()
             self.stream = torch.cuda.Stream()
-            if allocator is None:
-                a, f = _torch_allocator(self.stream)
-            else:
-                # caller's device allocator: (alloc(nbytes) -> pointer or None,
-                # free(pointer)); pointers must be 256-byte aligned
-                ua, uf = allocator
-                a = ALLOC_FN(lambda nbytes, _ctx: ua(int(nbytes)))
-                f = FREE_FN(lambda ptr, _ctx: uf(int(ptr)))
+            a, f = _torch_allocator(self.stream)
             self._keep += [a, f]
             opt.alloc, opt.free = a, f
             opt.cuda_stream = C.c_void_p(self.stream.cuda_stream)
