@@ -285,6 +285,28 @@ def test_edge_cases():
     assert e.value.status == -7
 
 
+def test_list_overflow_during_a_run_is_reported_and_recovered():
+    """A list capacity equal to the initial longest list and a hot lattice
+    rebuilt every step: a later build finds an atom with more neighbours, the
+    run reports MD_ERR_LIST_OVERFLOW at its next synchronising call (a sticky
+    device flag; the entries past the capacity are dropped, never written
+    out of bounds), and md_set_state of a state that fits restores a context
+    whose forces meet the oracle."""
+    hot = I.thermal_system(I.BCC_TA_LIKE, (6, 6, 6), 0.01, 3000.0, 17)
+    with binding.MD(hot, precision="mixed", persistent="off") as probe:
+        cap0 = probe.stats()["max_neighbors"]
+    with binding.MD(hot, precision="mixed", persistent="off", list_capacity=cap0, rebuild_every=1) as md:
+        assert md.stats()["list_capacity"] == cap0
+        with pytest.raises(binding.MDError) as e:
+            for _ in range(100):
+                md.step(5, 2.0)
+                md.energy()
+        assert e.value.status == -7
+        md.set_state(hot.pos, hot.vel, 0)
+        _, _, F, _, _ = oracle_eval(hot)
+        assert_forces(md.forces(), F, "mixed", "after recovery")
+
+
 def test_full_size_800k_mixed_forces():
     """799,496 atoms in the configuration the benchmark times: all forces
     against the oracle (which finishes this O(N) evaluation in seconds)."""
