@@ -20,8 +20,10 @@ MD timesteps per second (higher is better).
 After the timed region (rank 0, one GPU) the line also carries short legs
 measured in the same run: the plain FP64 GPU path on the same system
 (`fp64`, and the mixed/FP64 ratio), the half-list form (`half_list`), the
-512-replica batched launch (`batch`, atom-steps/s) and the oracle on all host
-cores (`cpu_baseline_all_cores`); --no-extras leaves them out.
+512-replica batched launch (`batch`, atom-steps/s), the force-matching
+gradient (`adjoint`: seconds per loss and gradient, and its agreement with
+finite differences) and the oracle on all host cores
+(`cpu_baseline_all_cores`); --no-extras leaves them out.
 
 --impl reference times the CPU oracle (the plain serial FP64 C reference)
 on a bounded sample of the same workload: one timestep per benchmark step.
@@ -276,7 +278,9 @@ def extra_legs(args, system, mixed_ts_per_s):
     """Short measurements beside the headline, in the same run: the plain
     FP64 GPU path and the half-list form on the same 799,496-atom system
     (device time of whole bench steps, CUDA events on the library's stream),
-    the 512-replica batched launch, and the oracle on all host cores."""
+    the 512-replica batched launch, one force-matching loss and gradient
+    (with its agreement with finite differences on 6 knots), and the oracle
+    on all host cores."""
     import torch
     from paper_2405_07898_gb300 import binding, inputs as I
 
@@ -321,6 +325,9 @@ def extra_legs(args, system, mixed_ts_per_s):
     out["batch"] = {"value": info["atoms"] * nsteps / (ms * 1e-3), "unit": "atom-steps/s",
                     "workload": "replicas_512_bcc_fcc_mixed", "replicas": info["replicas"], "atoms": info["atoms"],
                     "steps": nsteps, "ms": ms, "threads_per_block": info["threads_per_block"]}
+    # the differentiated form: one force-matching loss and its knot gradient
+    adj = adjoint_leg(reps=3, n_fd=6)
+    out["adjoint"] = {k: v for k, v in adj.items() if k not in ("higher_is_better",)}
     if not args.no_cpu_baseline:
         out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args)
     return out
@@ -448,12 +455,12 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
-def run_adjoint(args):
+def adjoint_leg(reps: int = 3, n_fd: int = 12):
     """Differentiation: force-matching loss over 64 BCC configurations of
     2,000 atoms and its gradient over 3 x 64 spline knots (adjoint kernels,
     FP64): seconds per loss+gradient evaluation, and the relative difference
-    of the gradient from central finite differences of the loss on a sample
-    of knots."""
+    of the gradient from central finite differences of the loss on a seeded
+    sample of n_fd knots."""
     import numpy as np
     import torch
     from paper_2405_07898_gb300 import autodiff, inputs as I
@@ -463,13 +470,12 @@ def run_adjoint(args):
     fm = autodiff.ForceMatch(prob)
     theta = prob.theta0.copy()
     fm.evaluate(theta, grad=True)
-    reps = 3
     t0 = time.perf_counter()
     for _ in range(reps):
         loss, g = fm.evaluate(theta, grad=True)
     t_eval = (time.perf_counter() - t0) / reps
     rng = np.random.default_rng(7898)
-    ks = rng.choice(len(theta), size=12, replace=False)
+    ks = rng.choice(len(theta), size=n_fd, replace=False)
     fd = []
     for k in ks:
         h = 1e-5 * max(abs(theta[k]), 1e-3)
@@ -480,10 +486,14 @@ def run_adjoint(args):
     fd = np.array(fd)
     err = float(np.linalg.norm(g[ks] - fd) / np.linalg.norm(fd))
     fm.close()
-    print(json.dumps({"workload": "force_match_64x2000_bcc", "metric": "s per loss+gradient",
-                      "value": t_eval, "unit": "s", "higher_is_better": False, "configs": len(prob.configs),
-                      "knots": int(len(theta)), "loss": float(loss),
-                      "gradient_vs_central_fd_rel_err_12_knots": err}), flush=True)
+    return {"workload": "force_match_64x2000_bcc", "metric": "s per loss+gradient", "value": t_eval, "unit": "s",
+            "higher_is_better": False, "configs": len(prob.configs), "knots": int(len(theta)),
+            "loss": float(loss), f"gradient_vs_central_fd_rel_err_{n_fd}_knots": err}
+
+
+def run_adjoint(args):
+    """The differentiation workload as its own JSON line (adjoint_leg)."""
+    print(json.dumps(adjoint_leg()), flush=True)
 
 
 def run_slab(args):
@@ -725,7 +735,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="leave out the FP64, half-list, batch and all-cores legs of the default line")
+                    help="leave out the FP64, half-list, batch, adjoint and all-cores legs of the default line")
     ap.add_argument("--batch-steps-extra", type=int, default=200,
                     help="steps of the batch leg in the default line")
     ap.add_argument("--half-list", action="store_true",
