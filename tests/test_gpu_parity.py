@@ -322,3 +322,23 @@ def test_full_size_800k_mixed_forces():
     _, _, F2, _, _ = oracle_eval(s, pos)
     with binding.MD(I.System(s.box, pos, s.vel, s.types, s.pot), precision="mixed") as md2:
         assert_forces(md2.forces(), F2, "mixed")
+
+
+@pytest.mark.parametrize("every", [1, 10, 1000])
+def test_profile_counts_the_list_builds(every):
+    """md_profile's per-kernel timing counts a step's rebuild span as a build
+    exactly when the device built a list in that step (its own counter), so
+    the average build time is over real builds: rebuild every step, every 10
+    steps, and (with dt = 0) never."""
+    s = I.thermal_system(I.BCC_TA_LIKE, (20, 20, 20), 0.02, 300.0, 23)
+    dt = 0.0 if every == 1000 else 2.0
+    with binding.MD(s, precision="mixed", persistent="off", rebuild_every=every) as md:
+        before = md.stats()["rebuilds"]
+        prof = md.profile(20, dt)
+        built = md.stats()["rebuilds"] - before
+        assert prof["rebuilds"] == built == {1: 20, 10: 2, 1000: 0}[every]
+        if built:
+            assert prof["rebuild_ms"] > 0.0
+        else:
+            assert prof["rebuild_ms"] == 0.0
+        assert prof["density_ms"] > 0.0 and prof["force_ms"] > 0.0
